@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the CCPR time-domain adjoint gradient on GB300.
+
+One benchmark step = one gradient evaluation of the whole hot path: forward Yee/CPML/CCPR run
+with the running DFT, adjoint run, and dF/drho over the design box.  Metric: Gcell-updates/s =
+2 * n_cells * n_time_steps / wall time per gradient.
+
+Default workload (config 2 of the paper-shaped workloads): 256^3 grid, 12-cell CPML, 4000 time
+steps, 128^3 design box with smooth seeded density blending air and a 3-pair CCPR metal,
+3 objective frequencies (500/600/700 nm), TF/SF plane wave along x, FP32 fields with FP64 DFT.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the problem does not need a
+collective); value = all ranks' cell-updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s Yee+CCPR fwd+adj FP32, % HBM roofline; p50/p99 grad latency"
+UNIT = "Gcell-updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--time-steps", type=int, default=0, help="override the workload's time steps")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-steps", type=int, default=16,
+                    help="time steps of the bounded oracle sample (CPU baseline / reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is None:
+        return
+    if device is not None:
+        dist.barrier(device_ids=[device])
+    else:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value, device=None):
+    """Max of a float over ranks (the job's wall time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=f"cuda:{device}" if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=f"cuda:{device}" if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------------
+def workload_and_config(args):
+    import synth
+    w = synth.workload(args.workload)
+    d = w["desc"]
+    if args.time_steps:
+        d["n_steps"] = args.time_steps
+    ncell = d["nx"] * d["ny"] * d["nz"]
+    dshape = synth.box_shape(d["design_box"])
+    poles = [len(w["m1"]["poles"][0]) + len(w["m2"]["poles"][0])]
+    cfg = {
+        "workload": {
+            "c1": "config 1: 32^3 Yee grid dx=5nm, 8-cell CPML, 1000 steps, z-dipole, 16^3 design, "
+                  "vacuum | 2-pair Drude-Lorentz metal, 600 nm, FP64",
+            "c2": "config 2: 256^3 Yee grid dx=5nm, 12-cell CPML, 4000 steps, 128^3 design with smooth "
+                  "seeded density, air | 3-pair CCPR metal, objective at 500/600/700 nm, TF/SF plane wave "
+                  "along x, FP32 fields + FP64 DFT",
+            "c3": "config 3: 512x512x384 grid, 16-cell CPML, 6000 steps, 256x256x192 design, 2-pair "
+                  "Lorentz dielectric | 4-pair metal, FP32",
+            "c4": "config 4: 64^3 grid, 2000 steps, 32^3 design, 2-pair metal, rho in [0.2,0.8]",
+        }[args.workload],
+        "grid": [d["nx"], d["ny"], d["nz"]], "time_steps": d["n_steps"], "design": list(dshape[::-1]),
+        "pole_pairs_total": poles[0], "n_freq": len(d["freqs_hz"]), "precision": d["precision"],
+        "dft_accumulators": "f64", "parallelism": f"replicas x{args.gpus}",
+    }
+    return w, cfg, ncell
+
+
+def footprint_bytes(w):
+    from paper_2305_00234_gb300 import fdtd_footprint_bytes
+    pt = [len(w["m1"]["poles"][k]) + len(w["m2"]["poles"][k]) for k in range(3)]
+    return fdtd_footprint_bytes(w["desc"], pt)
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("fdtd_kernels.cuh",):
+        with open(os.path.join(ROOT, "paper_2305_00234_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per E-kernel launch from a committed ncu summary, if taken on this kernel."""
+    p = os.path.join(ROOT, "profiles", "e_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    if j.get("kernel_hash") != kernel_hash():
+        return None
+    return j.get("per_launch_bytes", {}).get(workload)
+
+
+def cpu_baseline(args, w_full):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload (its first
+    cpu-sample-steps time steps, forward + adjoint + gradient), on the host cores."""
+    import copy
+
+    import oracle
+    w = copy.deepcopy(w_full)
+    w["desc"]["n_steps"] = args.cpu_sample_steps
+    d = w["desc"]
+    ncell = d["nx"] * d["ny"] * d["nz"]
+    t0 = time.perf_counter()
+    o = oracle.problem(w)
+    t1 = time.perf_counter()
+    o.forward()
+    o.adjoint()
+    o.gradient()
+    t2 = time.perf_counter()
+    o.close()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cu = 2.0 * ncell * d["n_steps"]
+    return {"value": cu / (t2 - t1) / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{args.workload} grid and materials, first {d['n_steps']} time steps of the forward "
+                      f"and adjoint runs + gradient ({cu:.3g} cell-updates, {t2 - t1:.1f} s; setup "
+                      f"{t1 - t0:.1f} s excluded)",
+            "seconds": t2 - t1}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    w, cfg, ncell = workload_and_config(args)
+    import copy
+
+    import oracle
+    ws = copy.deepcopy(w)
+    ws["desc"]["n_steps"] = args.cpu_sample_steps
+    o = oracle.problem(ws)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o.forward()
+        o.adjoint()
+        o.gradient()
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    o.close()
+    cu = 2.0 * ncell * args.cpu_sample_steps
+    value = cu * len(times) / sum(times) / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"each step: the {args.workload} workload's grid and materials for its first "
+              f"{args.cpu_sample_steps} time steps (forward + adjoint + gradient), FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    import paper_2305_00234_gb300 as lib
+    lib.load_library()
+    w, cfg, ncell = workload_and_config(args)
+    d = w["desc"]
+    M = d["n_steps"]
+    fp = footprint_bytes(w)
+    cfg["working_set_bytes"] = fp
+    cfg["l2"] = ("inputs larger than L2: working set %.2f GB vs 129 MB L2, no flush" % (fp / 1e9)
+                 if fp > L2_BYTES else "working set below L2: L2 flushed between steps")
+    stream = torch.cuda.current_stream()
+    p = lib.Problem(d, w["bg"], w["m1"], w["m2"], w["gamma"], stream=stream.cuda_stream)
+    rho_dev = torch.tensor(w["rho"], dtype=torch.float32, device=f"cuda:{local}")
+    grad_dev = torch.zeros(p.dshape, dtype=torch.float32, device=f"cuda:{local}")
+    p.set_density(rho_dev)
+    flush = None
+    if fp <= L2_BYTES:
+        flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def one_step():
+        p.forward()
+        p.adjoint()
+        p.gradient(grad_dev)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    # ---- timed region (device-resident inputs) ----
+    p.reset_timings()
+    p.set_profiling(True)
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(dist, local)
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        ev[s][0].record(stream)
+        one_step()
+        ev[s][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist, local)
+    clocks = sampler.stop()
+    p.set_profiling(False)
+    tim = p.timings()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    t_max = max_over_ranks(dist, elapsed_ms / 1e3, local)
+    cu_step = 2.0 * ncell * M
+    total_cu = sum_over_ranks(dist, cu_step * args.steps, local)
+    value = total_cu / t_max / 1e9
+    # dominant kernel (E update + CCPR + DFT): algorithmic bytes / average launch time
+    e_avg_s = tim["e_ms"] / max(tim["e_launches"], 1) / 1e3
+    h_avg_s = tim["h_ms"] / max(tim["h_launches"], 1) / 1e3
+    dft_avg_s = tim["dft_ms"] / max(tim["dft_launches"], 1) / 1e3
+    peak, peak_src = measured_peaks()
+    e_ach = tim["bytes_e_per_launch"] / e_avg_s / 1e9
+    h_ach = tim["bytes_h_per_launch"] / h_avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": f"e_kernel<{'float' if d['precision'] == 32 else 'double'}>",
+            "achieved": e_ach, "peak": peak, "unit": "GB/s", "frac": e_ach / peak,
+            "traffic": profiled_traffic(args.workload), "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": tim["bytes_e_per_launch"],
+            "avg_launch_ms": e_avg_s * 1e3,
+            "h_kernel": {"achieved": h_ach, "frac": h_ach / peak,
+                         "algorithmic_bytes_per_launch": tim["bytes_h_per_launch"],
+                         "avg_launch_ms": h_avg_s * 1e3},
+            "dft_kernel": {"achieved": tim["bytes_dft_per_launch"] / max(dft_avg_s, 1e-12) / 1e9,
+                           "frac": tim["bytes_dft_per_launch"] / max(dft_avg_s, 1e-12) / 1e9 / peak,
+                           "algorithmic_bytes_per_launch": tim["bytes_dft_per_launch"],
+                           "steps_per_launch": tim["dft_steps_per_launch"],
+                           "avg_launch_ms": dft_avg_s * 1e3},
+            "time_share": {"e": tim["e_ms"] / elapsed_ms, "h": tim["h_ms"] / elapsed_ms,
+                           "dft": tim["dft_ms"] / elapsed_ms, "grad": tim["grad_ms"] / elapsed_ms}}
+    launches = int(tim["launches"])
+    # ---- end to end through the public API with host buffers ----
+    rho_host = torch.tensor(w["rho"], dtype=torch.float32).pin_memory()
+    grad_host = torch.zeros(p.dshape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    barrier(dist, local)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        p.set_density(rho_host)
+        p.forward()
+        p.adjoint()
+        p.gradient(grad_host)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, local)
+    e2e_value = sum_over_ranks(dist, cu_step * args.e2e_steps, local) / e2e_s / 1e9
+    nd = int(np.prod(p.dshape))
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * nd, "d2h_bytes_per_step": 4 * nd,
+           "note": "per step: float32 density H2D from pinned memory, float32 gradient D2H to pinned "
+                   "memory (plus < 2 KB of gap DFT and adjoint coefficients)"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, w)
+    p.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if d["precision"] == 32 else "f64",
+                "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks,
+                "latency_ms": {"p50": statistics.median(per_step),
+                               "p99": float(np.percentile(per_step, 99)), "n": len(per_step),
+                               "note": "single-request gradient latency in the timed loop"}}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

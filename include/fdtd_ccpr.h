@@ -1,0 +1,189 @@
+/* fdtd_ccpr.h — C-ABI of the GB300 (sm_103a) CCPR time-domain adjoint gradient library.
+ *
+ * One handle = one gradient problem for density-based topology optimisation with dispersive
+ * materials (arXiv 2305.00234):
+ *   forward 3-D Yee FDTD run with CPML and the CCPR pole-current ADE, the density rho in [0,1]
+ *   blending two CCPR materials inside a design box (Methods, "Time-domain adjoint formulation",
+ *   Eqs. (eps_mixed), (sigma_mixed), (Poles_mixed), (Maxwells)); running DFTs of E over the
+ *   design box; a gap objective F = sum_f w_f sum_{gap samples} |Ehat(w_f)|^2 (frequency-domain
+ *   form of Eq. (Objective_analyitically_enhancement)); the adjoint run, i.e. the same solver
+ *   driven at the gap by the conjugated (time-reversed) objective derivative (SI Eq.
+ *   (AdjointSystem)); and dF/drho per design voxel from the forward and adjoint DFTs (three-term
+ *   structure of Eq. (Gradient_analytic), difference/average structure of Eq. (Gradient_FDTD)).
+ *
+ * Conventions (all calls):
+ *  - Grid: nx*ny*nz cells, arrays (nz, ny, nx) with x fastest.  Voxel (i,j,k) owns E_x(i+1/2,j,k),
+ *    E_y(i,j+1/2,k), E_z(i,j,k+1/2) (Yee layout, "FDTD implementation and design export"); those
+ *    samples take the voxel's material and density.  Outer walls are PEC behind the CPML.
+ *  - Time: dt = courant*dx/c0 (c0 = 299792458 m/s, mu0 = 1.25663706212e-6 H/m, eps0 =
+ *    1/(mu0 c0^2)); E at integer steps, H at half steps; n_steps steps per run.
+ *  - e^{j w t} convention (paper, below Eq. (CCPRModel)); DFT Ehat(w) = sum_{n=1..M} E^n e^{-j w n dt}.
+ *  - Boxes are half-open [i0,i1)x[j0,j1)x[k0,k1) given as {i0,i1,j0,j1,k0,k1}.
+ *  - Ownership: the library owns all device state.  Caller pointers are borrowed for the call
+ *    only.  on_device = 1 means a device pointer valid on the handle's stream (the stream passed
+ *    to fdtd_create_grid; NULL = the legacy default stream); 0 means a host pointer.
+ *  - Errors: every call returns a status and never throws.  fdtd_last_error() gives the text.
+ *    After FDTD_ERR_CUDA or FDTD_ERR_UNSTABLE the handle accepts only fdtd_destroy,
+ *    fdtd_last_error and fdtd_get_*.  A handle is not thread-safe; separate handles are.
+ *  - Call order: create -> set_materials -> set_density -> forward -> adjoint -> gradient.
+ *    set_materials/set_density invalidate earlier forward/adjoint results.
+ */
+#ifndef FDTD_CCPR_H
+#define FDTD_CCPR_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdtd_ctx* fdtd_handle;
+
+typedef enum {
+    FDTD_OK = 0,
+    FDTD_ERR_ARG = 1,       /* invalid argument or size mismatch */
+    FDTD_ERR_OOM = 2,       /* device allocation failed */
+    FDTD_ERR_CUDA = 3,      /* CUDA runtime error (handle is dead) */
+    FDTD_ERR_STATE = 4,     /* calls out of order */
+    FDTD_ERR_UNSTABLE = 5,  /* non-finite or exploding field detected (handle is dead) */
+    FDTD_ERR_TIMEOUT = 6,   /* a bounded device wait gave up */
+    FDTD_ERR_CANCELLED = 7  /* cancelled by fdtd_cancel */
+} fdtd_status;
+
+/* Grid, time stepping, boxes, objective frequencies and source.
+ *  cpml[6]: CPML thickness in cells on faces x-,x+,y-,y+,z-,z+ (the paper: 20 cells, "Technical
+ *    details of the optimization"; profile parameters are not given there).  CFS-CPML with
+ *    sigma = sigma_max d^m, kappa = 1+(kappa_max-1) d^m, a = a_max (1-d), d = depth fraction,
+ *    sigma_max = cpml_sigma_scale * 0.8 (m+1)/(eta0 dx).
+ *  precision: 32 (FP32 fields and pole currents) or 64 (all FP64).  DFT accumulators, the
+ *    gradient and the coefficient precompute are FP64 in both.
+ *  design_box must lie outside the CPML; gap_box inside design_box (gap voxels are fixed
+ *    background material, gradient 0 there).
+ *  n_freq in [1, 8] objective frequencies (Hz) with weights.
+ *  src_kind 0: soft point source on E_{src_comp} of voxel src_pos, drive added to (curl H) =
+ *    src_amp (eps0/dt) p((n+1/2) dt);  src_kind 1: one-sided TF/SF plane wave along +x, E_z/H_y,
+ *    first total-field plane x = src_pos[0] dx, incident field src_amp p(t) from a matched 1-D line.
+ *    p(t) = exp(-(t-t0)^2/(2 tau^2)) sin(2 pi f0 (t-t0)), tau = sqrt(2 ln 2)/(pi src_fwhm_hz),
+ *    t0 = src_t0 or 4 tau if src_t0 <= 0.
+ *  adj_tau: envelope of the 2F adjoint basis pulses g(t){cos,sin}(w_f (t - 4 adj_tau));
+ *    <= 0 selects the source's tau. */
+typedef struct {
+    int nx, ny, nz;
+    double dx;
+    double courant;
+    int n_steps;
+    int cpml[6];
+    double cpml_m, cpml_sigma_scale, cpml_kappa_max, cpml_a_max;
+    int precision;
+    int design_box[6];
+    int gap_box[6];
+    int n_freq;
+    const double* freqs_hz;
+    const double* freq_weights;
+    int src_kind;
+    int src_comp;
+    int src_pos[3];
+    double src_f0, src_fwhm_hz, src_t0, src_amp;
+    double adj_tau;
+} fdtd_grid_desc;
+
+/* One CCPR material (Eq. (CCPRModel)): per Cartesian component k, eps_inf[k], sigma[k] (S/m)
+ * and n_poles[k] pole pairs (a_p, c_p), each standing for c/(jw-a) + conj(c)/(jw-conj(a)); a in rad/s
+ * with Re(a) <= 0 and a != 0, c in 1/s.  Arrays are read during the call only. */
+typedef struct {
+    double eps_inf[3];
+    double sigma[3];
+    int n_poles[3];
+    const double* a_re[3];
+    const double* a_im[3];
+    const double* c_re[3];
+    const double* c_im[3];
+} fdtd_ccpr_material;
+
+/* Per-kernel device time, measured with CUDA events on the handle's stream while profiling is
+ * on (fdtd_set_profiling); launches = kernels this library launched since the last reset. */
+typedef struct {
+    double h_ms, e_ms, dft_ms, grad_ms;      /* summed device time per kernel kind */
+    long long h_launches, e_launches, dft_launches, grad_launches;
+    long long launches;                      /* every kernel launch of this library */
+    /* algorithmic bytes per launch: each state word read once and written once */
+    double bytes_h_per_launch, bytes_e_per_launch, bytes_dft_per_launch, bytes_grad_per_launch;
+    double dft_steps_per_launch;             /* time steps folded into one DFT launch */
+} fdtd_timings;
+
+/* Create a problem on the given CUDA stream (cudaStream_t; NULL = default stream) of the current
+ * device.  Validates the description and allocates every device buffer (footprint as returned
+ * by fdtd_footprint_bytes).  Errors: FDTD_ERR_ARG (invalid desc), FDTD_ERR_OOM, FDTD_ERR_CUDA. */
+fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd_handle* out);
+
+/* Device bytes a handle with this description and these pole counts would allocate
+ * (p_total[k] = poles of m1 + m2 on component k).  For admission control; allocates nothing. */
+fdtd_status fdtd_footprint_bytes(const fdtd_grid_desc* desc, const int p_total[3], size_t* bytes);
+
+/* Materials: bg outside the design box and in the gap (must be non-dispersive: n_poles = 0);
+ * m1 at rho = 0 and m2 at rho = 1 inside it (both materials' poles are kept, weighted 1-rho and
+ * rho; Eq. (Poles_mixed)); gamma: conductivity damping rho(1-rho)gamma (Eq. (sigma_mixed)).
+ * Pole coefficients alpha = e^{a dt}, beta = eps0 c (e^{a dt}-1)/(2a) are computed here in FP64.
+ * Errors: FDTD_ERR_ARG (pole counts > 16 per component in total, Re a > 0, non-positive update
+ * denominator at rho = 0 or 1). */
+fdtd_status fdtd_set_materials(fdtd_handle h, const fdtd_ccpr_material* bg, const fdtd_ccpr_material* m1,
+                               const fdtd_ccpr_material* m2, double gamma);
+
+/* Density on the design box, (dnz, dny, dnx) x fastest, n = dnx*dny*dnz values in [0, 1];
+ * dtype 0 = float32, 1 = float64.  Values outside [0,1] or non-finite: FDTD_ERR_ARG (checked on
+ * the device when on_device = 1). */
+fdtd_status fdtd_set_density(fdtd_handle h, const void* rho, size_t n, int dtype, int on_device);
+
+/* Forward run: zero state, n_steps steps with the forward source, forward DFT over the design
+ * box.  F_out (host, nullable) receives the objective; gap_dft_out (host, nullable) receives the
+ * gap DFT, (F, 3, gnz, gny, gnx) complex as interleaved (re, im) doubles.
+ * Errors: FDTD_ERR_STATE before set_density, FDTD_ERR_UNSTABLE, FDTD_ERR_CUDA. */
+fdtd_status fdtd_forward(fdtd_handle h, double* F_out, double* gap_dft_out);
+
+/* Adjoint run (requires forward): builds the adjoint drive at every gap sample g as
+ * sum_q r_{g,q} b_q(t) over the 2F basis pulses, r_g solving (2F x 2F, FP64 on the host)
+ * sum_q r_{g,q} sum_{n<M} b_q((n+1/2)dt) e^{-j w_f n dt} = w_f conj(Ehat_g(w_f)), then runs the
+ * same solver and accumulates the adjoint DFT. */
+fdtd_status fdtd_adjoint(fdtd_handle h);
+
+/* Gradient (requires adjoint): per design voxel
+ *   dF/drho = -sum_{owned k} sum_f 2 Re{ dY_k/drho(w_f) Ehat_k(w_f) Lambda_k(w_f) },
+ *   dY/drho = (1/dt)[eps0 d_eps (z-1) + (d_sigma + (1-2rho) gamma) dt (z+1)/2
+ *                    + (z-1)(sum_{m2}(h+hb) - sum_{m1}(h+hb))],  z = e^{j w dt},
+ *   h = beta (z+1)/(z-alpha), hb the same with conj(alpha), conj(beta); 0 on gap voxels.
+ * grad: n = design voxels, dtype 0 float32 / 1 float64, host or device.  grad_norm2_out
+ * (nullable, host) receives sum of squares (FP64). */
+fdtd_status fdtd_gradient(fdtd_handle h, void* grad, size_t n, int dtype, int on_device);
+fdtd_status fdtd_gradient_norm(fdtd_handle h, double* grad_norm2_out);
+
+/* Parity/inspection (host buffers, synchronous).
+ *  fdtd_get_field: which 0..5 = Ex,Ey,Ez,Hx,Hy,Hz after the last run, n = nx*ny*nz doubles.
+ *  fdtd_get_dft: adjoint 0/1, n_doubles = 2*F*3*nd, layout (F,3,dnz,dny,dnx) complex interleaved.
+ *  fdtd_get_index_map: which 0: (3,nz,ny,nx) per E sample: bits 0-1 voxel class (0 background,
+ *    1 design, 2 gap), bit 2 PEC-fixed, bits 3/4 inside the CPML of derivative axis (c+1)%3 /
+ *    (c+2)%3 at the sample's integer position, bit 5 forward dipole sample; 1: (3,nz,ny,nx) per H
+ *    sample, bits 3/4 for half-integer positions; 2: per voxel design index or -1; 3: per voxel
+ *    gap index or -1.  Computed on the device by the same index helpers the kernels use. */
+fdtd_status fdtd_get_field(fdtd_handle h, int which, double* dst, size_t n);
+fdtd_status fdtd_get_dft(fdtd_handle h, int adjoint, double* dst, size_t n_doubles);
+fdtd_status fdtd_get_index_map(fdtd_handle h, int which, int32_t* dst, size_t n);
+
+/* Profiling: when on, runs launch kernels one by one (no CUDA graph) with CUDA events around
+ * each kernel; fdtd_get_timings returns the sums since fdtd_reset_timings. */
+fdtd_status fdtd_set_profiling(fdtd_handle h, int on);
+fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out);
+fdtd_status fdtd_reset_timings(fdtd_handle h);
+
+/* Scalars: dt (s), design voxel count, gap voxel count, device footprint (bytes). */
+fdtd_status fdtd_get_info(fdtd_handle h, double* dt, size_t* n_design, size_t* n_gap, size_t* device_bytes);
+
+/* Request that a run in progress on another host thread stop at the next chunk boundary
+ * (it returns FDTD_ERR_CANCELLED).  The only call that may come from another thread. */
+fdtd_status fdtd_cancel(fdtd_handle h);
+
+const char* fdtd_last_error(fdtd_handle h);
+fdtd_status fdtd_destroy(fdtd_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,278 @@
+"""ctypes binding of ``libfdtdccpr.so`` (C-ABI in include/fdtd_ccpr.h).
+
+Argument marshalling only: every step of the gradient evaluation runs in the library's CUDA
+kernels.  If the library has not been built this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libfdtdccpr.so")
+
+FDTD_OK = 0
+STATUS = {0: "FDTD_OK", 1: "FDTD_ERR_ARG", 2: "FDTD_ERR_OOM", 3: "FDTD_ERR_CUDA", 4: "FDTD_ERR_STATE",
+          5: "FDTD_ERR_UNSTABLE", 6: "FDTD_ERR_TIMEOUT", 7: "FDTD_ERR_CANCELLED"}
+
+EXPORTS = ("fdtd_create_grid", "fdtd_footprint_bytes", "fdtd_set_materials", "fdtd_set_density",
+           "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gradient_norm", "fdtd_get_field",
+           "fdtd_get_dft", "fdtd_get_index_map", "fdtd_set_profiling", "fdtd_get_timings",
+           "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy")
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("courant", C.c_double), ("n_steps", C.c_int),
+                ("cpml", C.c_int * 6),
+                ("cpml_m", C.c_double), ("cpml_sigma_scale", C.c_double),
+                ("cpml_kappa_max", C.c_double), ("cpml_a_max", C.c_double),
+                ("precision", C.c_int),
+                ("design_box", C.c_int * 6), ("gap_box", C.c_int * 6),
+                ("n_freq", C.c_int), ("freqs_hz", C.POINTER(C.c_double)),
+                ("freq_weights", C.POINTER(C.c_double)),
+                ("src_kind", C.c_int), ("src_comp", C.c_int), ("src_pos", C.c_int * 3),
+                ("src_f0", C.c_double), ("src_fwhm_hz", C.c_double), ("src_t0", C.c_double),
+                ("src_amp", C.c_double), ("adj_tau", C.c_double)]
+
+
+class Material(C.Structure):
+    _fields_ = [("eps_inf", C.c_double * 3), ("sigma", C.c_double * 3), ("n_poles", C.c_int * 3),
+                ("a_re", C.POINTER(C.c_double) * 3), ("a_im", C.POINTER(C.c_double) * 3),
+                ("c_re", C.POINTER(C.c_double) * 3), ("c_im", C.POINTER(C.c_double) * 3)]
+
+
+class Timings(C.Structure):
+    _fields_ = [("h_ms", C.c_double), ("e_ms", C.c_double), ("dft_ms", C.c_double),
+                ("grad_ms", C.c_double),
+                ("h_launches", C.c_longlong), ("e_launches", C.c_longlong),
+                ("dft_launches", C.c_longlong), ("grad_launches", C.c_longlong),
+                ("launches", C.c_longlong),
+                ("bytes_h_per_launch", C.c_double), ("bytes_e_per_launch", C.c_double),
+                ("bytes_dft_per_launch", C.c_double), ("bytes_grad_per_launch", C.c_double),
+                ("dft_steps_per_launch", C.c_double)]
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library():
+    """Load the in-tree CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FdtdError(3, f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    P, vp, sz, d, i = C.POINTER, C.c_void_p, C.c_size_t, C.c_double, C.c_int
+    sig = {
+        "fdtd_create_grid": [P(GridDesc), vp, P(vp)],
+        "fdtd_footprint_bytes": [P(GridDesc), P(C.c_int), P(sz)],
+        "fdtd_set_materials": [vp, P(Material), P(Material), P(Material), d],
+        "fdtd_set_density": [vp, vp, sz, i, i],
+        "fdtd_forward": [vp, P(d), P(d)],
+        "fdtd_adjoint": [vp],
+        "fdtd_gradient": [vp, vp, sz, i, i],
+        "fdtd_gradient_norm": [vp, P(d)],
+        "fdtd_get_field": [vp, i, P(d), sz],
+        "fdtd_get_dft": [vp, i, P(d), sz],
+        "fdtd_get_index_map": [vp, i, P(C.c_int32), sz],
+        "fdtd_set_profiling": [vp, i],
+        "fdtd_get_timings": [vp, P(Timings)],
+        "fdtd_reset_timings": [vp],
+        "fdtd_get_info": [vp, P(d), P(sz), P(sz), P(sz)],
+        "fdtd_cancel": [vp],
+        "fdtd_last_error": [vp],
+        "fdtd_destroy": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name == "fdtd_last_error" else C.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_desc(desc, keep):
+    """GridDesc from a description dict (keys as in the C struct); arrays kept alive in `keep`."""
+    g = GridDesc()
+    for key in ("nx", "ny", "nz", "n_steps", "precision", "src_kind", "src_comp"):
+        setattr(g, key, int(desc[key]))
+    for key in ("dx", "courant", "cpml_m", "cpml_sigma_scale", "cpml_kappa_max", "cpml_a_max",
+                "src_f0", "src_fwhm_hz", "src_t0", "src_amp", "adj_tau"):
+        setattr(g, key, float(desc[key]))
+    for key, n in (("cpml", 6), ("design_box", 6), ("gap_box", 6), ("src_pos", 3)):
+        for q in range(n):
+            getattr(g, key)[q] = int(desc[key][q])
+    f = np.ascontiguousarray(desc["freqs_hz"], dtype=np.float64)
+    w = np.ascontiguousarray(desc["freq_weights"], dtype=np.float64)
+    keep += [f, w]
+    g.n_freq = f.size
+    g.freqs_hz = _dptr(f)
+    g.freq_weights = _dptr(w)
+    return g
+
+
+def make_material(m, keep):
+    s = Material()
+    for k in range(3):
+        s.eps_inf[k] = float(m["eps_inf"][k])
+        s.sigma[k] = float(m["sigma"][k])
+        poles = m["poles"][k]
+        s.n_poles[k] = len(poles)
+        arrs = [np.ascontiguousarray([complex(a).real for a, _ in poles] or [0.0]),
+                np.ascontiguousarray([complex(a).imag for a, _ in poles] or [0.0]),
+                np.ascontiguousarray([complex(c).real for _, c in poles] or [0.0]),
+                np.ascontiguousarray([complex(c).imag for _, c in poles] or [0.0])]
+        keep += arrs
+        s.a_re[k], s.a_im[k], s.c_re[k], s.c_im[k] = (_dptr(a) for a in arrs)
+    return s
+
+
+def _check(h, rc, what):
+    if rc != FDTD_OK:
+        msg = load_library().fdtd_last_error(h)
+        raise FdtdError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+
+# ---- same names as the C-ABI (thin marshalling) ----------------------------------------------
+
+def fdtd_create_grid(desc, stream=None):
+    lib = load_library()
+    keep = []
+    g = make_desc(desc, keep)
+    h = C.c_void_p()
+    rc = lib.fdtd_create_grid(C.byref(g), C.c_void_p(stream or 0), C.byref(h))
+    if rc != FDTD_OK:
+        raise FdtdError(rc, "fdtd_create_grid: invalid description or allocation failure")
+    return h
+
+
+def fdtd_footprint_bytes(desc, p_total):
+    lib = load_library()
+    keep = []
+    g = make_desc(desc, keep)
+    pt = (C.c_int * 3)(*[int(x) for x in p_total])
+    out = C.c_size_t()
+    rc = lib.fdtd_footprint_bytes(C.byref(g), pt, C.byref(out))
+    if rc != FDTD_OK:
+        raise FdtdError(rc, "fdtd_footprint_bytes")
+    return out.value
+
+
+def fdtd_set_materials(h, bg, m1, m2, gamma=0.0):
+    keep = []
+    b, a1, a2 = make_material(bg, keep), make_material(m1, keep), make_material(m2, keep)
+    _check(h, load_library().fdtd_set_materials(h, C.byref(b), C.byref(a1), C.byref(a2),
+                                                 float(gamma)), "fdtd_set_materials")
+
+
+def _buffer(x):
+    """(pointer, n, dtype code, on_device, keepalive) for a numpy array or torch tensor."""
+    if hasattr(x, "data_ptr"):                  # torch tensor
+        import torch
+        if x.dtype not in (torch.float32, torch.float64):
+            raise TypeError("float32 or float64 tensor expected")
+        if not x.is_contiguous():
+            raise ValueError("contiguous tensor expected")
+        return x.data_ptr(), x.numel(), 0 if x.dtype == torch.float32 else 1, int(x.is_cuda), x
+    a = np.ascontiguousarray(x)
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    return a.ctypes.data, a.size, 0 if a.dtype == np.float32 else 1, 0, a
+
+
+def fdtd_set_density(h, rho):
+    p, n, dt, dev, keep = _buffer(rho)
+    _check(h, load_library().fdtd_set_density(h, C.c_void_p(p), n, dt, dev), "fdtd_set_density")
+
+
+def fdtd_forward(h, n_gap_doubles=0):
+    F = C.c_double()
+    g = np.zeros(max(n_gap_doubles, 1), dtype=np.float64)
+    _check(h, load_library().fdtd_forward(h, C.byref(F), _dptr(g) if n_gap_doubles else None),
+           "fdtd_forward")
+    return F.value, g[:n_gap_doubles]
+
+
+def fdtd_adjoint(h):
+    _check(h, load_library().fdtd_adjoint(h), "fdtd_adjoint")
+
+
+def fdtd_gradient(h, out):
+    p, n, dt, dev, keep = _buffer(out)
+    _check(h, load_library().fdtd_gradient(h, C.c_void_p(p), n, dt, dev), "fdtd_gradient")
+    return out
+
+
+def fdtd_gradient_norm(h):
+    v = C.c_double()
+    _check(h, load_library().fdtd_gradient_norm(h, C.byref(v)), "fdtd_gradient_norm")
+    return v.value
+
+
+def fdtd_get_field(h, which, n):
+    a = np.zeros(n, dtype=np.float64)
+    _check(h, load_library().fdtd_get_field(h, which, _dptr(a), n), "fdtd_get_field")
+    return a
+
+
+def fdtd_get_dft(h, adjoint, n_doubles):
+    a = np.zeros(n_doubles, dtype=np.float64)
+    _check(h, load_library().fdtd_get_dft(h, int(adjoint), _dptr(a), n_doubles), "fdtd_get_dft")
+    return a
+
+
+def fdtd_get_index_map(h, which, n):
+    a = np.zeros(n, dtype=np.int32)
+    _check(h, load_library().fdtd_get_index_map(h, which, a.ctypes.data_as(C.POINTER(C.c_int32)), n),
+           "fdtd_get_index_map")
+    return a
+
+
+def fdtd_set_profiling(h, on):
+    _check(h, load_library().fdtd_set_profiling(h, int(bool(on))), "fdtd_set_profiling")
+
+
+def fdtd_get_timings(h):
+    t = Timings()
+    _check(h, load_library().fdtd_get_timings(h, C.byref(t)), "fdtd_get_timings")
+    return {k: getattr(t, k) for k, _ in Timings._fields_}
+
+
+def fdtd_reset_timings(h):
+    _check(h, load_library().fdtd_reset_timings(h), "fdtd_reset_timings")
+
+
+def fdtd_get_info(h):
+    dt, nd, ng, b = C.c_double(), C.c_size_t(), C.c_size_t(), C.c_size_t()
+    _check(h, load_library().fdtd_get_info(h, C.byref(dt), C.byref(nd), C.byref(ng), C.byref(b)),
+           "fdtd_get_info")
+    return {"dt": dt.value, "n_design": nd.value, "n_gap": ng.value, "device_bytes": b.value}
+
+
+def fdtd_cancel(h):
+    _check(h, load_library().fdtd_cancel(h), "fdtd_cancel")
+
+
+def fdtd_last_error(h):
+    m = load_library().fdtd_last_error(h)
+    return m.decode() if m else ""
+
+
+def fdtd_destroy(h):
+    if h:
+        load_library().fdtd_destroy(h)

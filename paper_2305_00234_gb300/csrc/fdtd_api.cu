@@ -1,0 +1,1253 @@
+// Host implementation of the C-ABI declared in include/fdtd_ccpr.h.
+//
+// Everything that is not per-cell work happens here in FP64 on the host, once per call:
+// CPML profiles, CCPR pole coefficients alpha = e^{a dt}, beta = eps0 c (e^{a dt}-1)/(2a),
+// update denominators, source waveforms (including the matched 1-D line of the TF/SF plane
+// wave), DFT phase tables, the 2F x 2F adjoint basis solve and the gradient constants
+// dY/drho(w_f).  The per-cell work runs in the kernels of fdtd_kernels.cuh.
+//
+// A run enqueues CUDA graphs of up to kGraphSteps (H, E) step pairs on a private stream; the
+// caller's stream is fenced with events before and after, so device pointers passed with
+// on_device = 1 are ordered with the caller's work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fdtd_ccpr.h"
+#include "fdtd_launch.h"
+
+namespace {
+
+using cd = std::complex<double>;
+using fdtd::cpx;
+using fdtd::DParams;
+using fdtd::GParams;
+using fdtd::KParams;
+using fdtd::PoleTable;
+
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+const double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+const double kPi = 3.14159265358979323846;
+constexpr int kGraphSteps = fdtd::kMaxSnap;   // one DFT block per captured graph
+constexpr int kChunkSteps = 512;
+
+struct Err {
+    fdtd_status code;
+    std::string msg;
+};
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) throw Err{FDTD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+[[noreturn]] void arg_error(const std::string& m) { throw Err{FDTD_ERR_ARG, m}; }
+
+// e^{z} - 1 without cancellation for small |z|.
+cd expm1c(cd z)
+{
+    const double x = z.real(), y = z.imag();
+    const double s = std::sin(0.5 * y);
+    return cd(std::expm1(x) * std::cos(y) - 2.0 * s * s, std::exp(x) * std::sin(y));
+}
+
+struct Pole {
+    cd a, c;
+};
+
+struct Material {
+    double eps[3] = {1, 1, 1}, sig[3] = {0, 0, 0};
+    std::vector<Pole> poles[3];
+};
+
+Material import_material(const fdtd_ccpr_material* m, const char* what)
+{
+    if (!m) arg_error(std::string(what) + ": null material");
+    Material out;
+    for (int k = 0; k < 3; ++k) {
+        out.eps[k] = m->eps_inf[k];
+        out.sig[k] = m->sigma[k];
+        if (!std::isfinite(out.eps[k]) || !std::isfinite(out.sig[k])) arg_error(std::string(what) + ": non-finite eps/sigma");
+        if (m->n_poles[k] < 0 || m->n_poles[k] > fdtd::kMaxPoles) arg_error(std::string(what) + ": bad pole count");
+        for (int p = 0; p < m->n_poles[k]; ++p) {
+            Pole q{cd(m->a_re[k][p], m->a_im[k][p]), cd(m->c_re[k][p], m->c_im[k][p])};
+            if (!(q.a.real() <= 0.0) || q.a == cd(0.0, 0.0)) arg_error(std::string(what) + ": pole with Re(a) > 0 or a = 0");
+            if (!std::isfinite(q.c.real()) || !std::isfinite(q.c.imag())) arg_error(std::string(what) + ": non-finite residue");
+            out.poles[k].push_back(q);
+        }
+    }
+    return out;
+}
+
+// CFS-CPML coefficients at position u (cells) along an axis of n cells with lo/hi layers.
+void pml_point(const fdtd_grid_desc& d, double dt, int lo, int hi, int n, double u, double* kinv, double* b, double* c)
+{
+    double depth = 0.0;
+    if (lo > 0 && u < lo)
+        depth = (lo - u) / lo;
+    else if (hi > 0 && u > n - hi)
+        depth = (u - (n - hi)) / hi;
+    if (depth <= 0.0) {
+        *kinv = 1.0;
+        *b = 1.0;
+        *c = 0.0;
+        return;
+    }
+    const double eta0 = kMu0 * kC0;
+    const double smax = d.cpml_sigma_scale * 0.8 * (d.cpml_m + 1.0) / (eta0 * d.dx);
+    const double gm = std::pow(depth, d.cpml_m);
+    const double sig = smax * gm;
+    const double kap = 1.0 + (d.cpml_kappa_max - 1.0) * gm;
+    const double al = d.cpml_a_max * (1.0 - depth);
+    *kinv = 1.0 / kap;
+    *b = std::exp(-(sig / kap + al) * dt / kEps0);
+    *c = sig > 0.0 ? sig * (*b - 1.0) / (sig * kap + kap * kap * al) : 0.0;
+}
+
+double src_tau(const fdtd_grid_desc& d) { return std::sqrt(2.0 * std::log(2.0)) / (kPi * d.src_fwhm_hz); }
+
+double src_pulse(const fdtd_grid_desc& d, double t)
+{
+    const double tau = src_tau(d);
+    const double t0 = d.src_t0 > 0.0 ? d.src_t0 : 4.0 * tau;
+    const double x = t - t0;
+    return std::exp(-x * x / (2.0 * tau * tau)) * std::sin(2.0 * kPi * d.src_f0 * x);
+}
+
+bool box_empty(const int* b) { return b[1] <= b[0] || b[3] <= b[2] || b[5] <= b[4]; }
+
+long long box_count(const int* b) { return box_empty(b) ? 0 : (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]); }
+
+void validate(const fdtd_grid_desc& d)
+{
+    const int n[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 4 || n[a] > 65535) arg_error("grid axis size out of [4, 65535]");
+        if (d.cpml[2 * a] < 0 || d.cpml[2 * a + 1] < 0 || d.cpml[2 * a] + d.cpml[2 * a + 1] > n[a] - 2)
+            arg_error("bad CPML thickness");
+    }
+    if ((long long)d.nx * d.ny * d.nz > (1LL << 31) - 1) arg_error("grid larger than 2^31 cells");
+    if (!(d.dx > 0.0) || !(d.courant > 0.0) || !(d.courant <= 1.0 / std::sqrt(3.0) + 1e-12))
+        arg_error("dx must be > 0 and 0 < courant <= 1/sqrt(3)");
+    if (d.n_steps < 1) arg_error("n_steps must be >= 1");
+    if (d.precision != 32 && d.precision != 64) arg_error("precision must be 32 or 64");
+    if (d.n_freq < 1 || d.n_freq > fdtd::kMaxFreq || !d.freqs_hz) arg_error("n_freq must be in [1, 8]");
+    for (int f = 0; f < d.n_freq; ++f)
+        if (!(d.freqs_hz[f] > 0.0) || (d.freq_weights && !std::isfinite(d.freq_weights[f]))) arg_error("bad frequency/weight");
+    if (!(d.cpml_m >= 0.0) || !(d.cpml_kappa_max >= 1.0) || !(d.cpml_a_max >= 0.0) || !(d.cpml_sigma_scale >= 0.0))
+        arg_error("bad CPML profile parameters");
+    const int* db = d.design_box;
+    const int* gb = d.gap_box;
+    if (!box_empty(db)) {
+        for (int a = 0; a < 3; ++a)
+            if (db[2 * a] < d.cpml[2 * a] || db[2 * a + 1] > n[a] - d.cpml[2 * a + 1] || db[2 * a] >= db[2 * a + 1])
+                arg_error("design box must lie inside the grid and outside the CPML");
+        if (box_count(db) > (1LL << 31) - 1) arg_error("design box too large");
+    }
+    if (!box_empty(gb)) {
+        if (box_empty(db)) arg_error("gap box without a design box");
+        for (int a = 0; a < 3; ++a)
+            if (gb[2 * a] < db[2 * a] || gb[2 * a + 1] > db[2 * a + 1]) arg_error("gap box must lie inside the design box");
+    }
+    if (d.src_kind == 0) {
+        for (int a = 0; a < 3; ++a)
+            if (d.src_pos[a] < 0 || d.src_pos[a] >= n[a]) arg_error("dipole outside the grid");
+        if (d.src_comp < 0 || d.src_comp > 2) arg_error("bad dipole component");
+    } else if (d.src_kind == 1) {
+        if (d.src_pos[0] < d.cpml[0] + 1 || d.src_pos[0] >= d.nx - d.cpml[1]) arg_error("TF/SF plane must lie outside the x CPML");
+    } else {
+        arg_error("src_kind must be 0 (dipole) or 1 (TF/SF plane)");
+    }
+    if (!(d.src_fwhm_hz > 0.0) || !(d.src_f0 >= 0.0) || !std::isfinite(d.src_amp)) arg_error("bad source parameters");
+}
+
+size_t footprint(const fdtd_grid_desc& d, const int ptot[3])
+{
+    const size_t ts = d.precision == 64 ? 8 : 4;
+    const size_t ncell = (size_t)d.nx * d.ny * d.nz;
+    const size_t nd = (size_t)box_count(d.design_box);
+    const size_t ng = (size_t)box_count(d.gap_box);
+    const int n[3] = {d.nx, d.ny, d.nz};
+    size_t b = 6 * ncell * ts;                                        // E, H
+    for (int a = 0; a < 3; ++a) {                                     // psi: 2 E + 2 H components per axis
+        const size_t w = (size_t)d.cpml[2 * a] + d.cpml[2 * a + 1];
+        b += 4 * (ncell / n[a]) * w * ts + 8 * w * ts;
+    }
+    b += nd * ts;                                                     // rho
+    for (int k = 0; k < 3; ++k) b += nd * (size_t)ptot[k] * 2 * ts;   // Q
+    b += 2 * nd * 3 * (size_t)d.n_freq * 16;                          // forward + adjoint DFT
+    b += (size_t)fdtd::kMaxSnap * 3 * nd * ts + nd * 8;               // DFT snapshot ring, staging
+    b += nd * 8 + ((nd + 255) / 256 + 1) * 8;                         // gradient + partials
+    b += ((size_t)d.n_steps + 1) * d.n_freq * 2 * ts;                 // phase table
+    b += (size_t)d.n_steps * (2 * fdtd::kMaxBasis + 2) * ts;          // source waves, TF/SF tables
+    b += (ng * 3 * fdtd::kMaxBasis + 3) * ts + ng * 3 * d.n_freq * 16;
+    b += sizeof(PoleTable<double>) + 256;
+    return b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Typed solver
+// ---------------------------------------------------------------------------------------------
+struct SolverBase {
+    virtual ~SolverBase() = default;
+};
+
+struct fdtd_ctx {
+    fdtd_grid_desc d{};
+    std::vector<double> freqs, weights;
+    cudaStream_t user = nullptr, work = nullptr;
+    cudaEvent_t fence = nullptr;
+    int device = 0;
+    double dt = 0;
+    size_t ncell = 0, nd = 0, ngap = 0;
+    int dn[3] = {0, 0, 0}, gn[3] = {0, 0, 0};
+    bool has_mat = false, has_rho = false, has_fwd = false, has_adj = false, has_grad = false, dead = false;
+    std::string err;
+    std::atomic<int> cancel{0};
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    fdtd_timings tim{};
+    std::unique_ptr<SolverBase> impl;
+
+    void* alloc(size_t n)
+    {
+        void* p = nullptr;
+        if (n == 0) n = 16;
+        if (cudaMalloc(&p, n) != cudaSuccess) {
+            cudaGetLastError();
+            throw Err{FDTD_ERR_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
+        }
+        allocs.push_back(p);
+        bytes += n;
+        return p;
+    }
+    void free_all()
+    {
+        for (void* p : allocs) cudaFree(p);
+        allocs.clear();
+    }
+};
+
+template <typename T>
+struct Solver : SolverBase {
+    fdtd_ctx* c;
+    KParams<T> base{};              // shared part of the kernel parameters
+    KParams<T> pf{}, pa{};          // forward / adjoint
+    T* src_r[2] = {nullptr, nullptr};
+    T* src_wave[2] = {nullptr, nullptr};
+    T* einc = nullptr;
+    T* hinc = nullptr;
+    T* rho = nullptr;
+    PoleTable<T>* poles = nullptr;
+    double2* dft[2] = {nullptr, nullptr};
+    using V2 = typename fdtd::vec2_of<T>::type;
+    V2* phase = nullptr;
+    T* snap = nullptr;
+    void* staging = nullptr;
+    DParams<T> dp[2]{};             // forward / adjoint DFT kernel parameters
+    int bucket = 16;
+    double2* gapbuf = nullptr;
+    double2* AB = nullptr;
+    double* grad = nullptr;
+    double* partial = nullptr;
+    unsigned* counter = nullptr;
+    int* ctl = nullptr;
+    int ptot[3] = {0, 0, 0};
+    std::vector<double2> ab_host;
+    std::vector<double> gap_dft;     // host copy of the forward gap DFT, (f,c,gv) complex
+    double adj_cond = 0.0;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mode][full, remainder]
+
+    explicit Solver(fdtd_ctx* ctx) : c(ctx) {}
+    ~Solver() override
+    {
+        for (auto& g : graph)
+            for (auto& x : g)
+                if (x) cudaGraphExecDestroy(x);
+    }
+
+    T* talloc(size_t n) { return (T*)c->alloc(n * sizeof(T)); }
+
+    void allocate(const int p_total[3])
+    {
+        const fdtd_grid_desc& d = c->d;
+        KParams<T>& p = base;
+        p.nx = d.nx;
+        p.ny = d.ny;
+        p.nz = d.nz;
+        p.plane = (long long)d.nx * d.ny;
+        p.ncell = p.plane * d.nz;
+        std::memcpy(p.db, d.design_box, sizeof p.db);
+        std::memcpy(p.gb, d.gap_box, sizeof p.gb);
+        if (box_empty(p.db)) std::fill(p.db, p.db + 6, 0);
+        if (box_empty(p.gb)) std::fill(p.gb, p.gb + 6, 0);
+        p.dnx = c->dn[0];
+        p.dny = c->dn[1];
+        p.dplane = (long long)c->dn[0] * c->dn[1];
+        p.nd = (long long)c->nd;
+        p.gnx = c->gn[0];
+        p.gny = c->gn[1];
+        p.gplane = (long long)c->gn[0] * c->gn[1];
+        const int n[3] = {d.nx, d.ny, d.nz};
+        for (int a = 0; a < 3; ++a) {
+            p.cpl[a] = d.cpml[2 * a];
+            p.cph[a] = d.cpml[2 * a + 1];
+            p.W[a] = p.cpl[a] + p.cph[a];
+        }
+        for (int cc = 0; cc < 3; ++cc) {
+            p.E[cc] = talloc(c->ncell);
+            p.H[cc] = talloc(c->ncell);
+            for (int t = 0; t < 2; ++t) {
+                const int a = (cc + 1 + t) % 3;
+                const size_t m = (size_t)(c->ncell / n[a]) * p.W[a];
+                p.psiE[cc][t] = talloc(m);
+                p.psiH[cc][t] = talloc(m);
+            }
+        }
+        // CPML tables {1/kappa, b, c, 0} per slab index
+        for (int a = 0; a < 3; ++a) {
+            const int W = p.W[a];
+            std::vector<T> te(4 * std::max(W, 1), T(0)), th(4 * std::max(W, 1), T(0));
+            for (int s = 0; s < W; ++s) {
+                const int l = s < p.cpl[a] ? s : n[a] - p.cph[a] + (s - p.cpl[a]);
+                double ki, b, cc2;
+                pml_point(d, c->dt, p.cpl[a], p.cph[a], n[a], (double)l, &ki, &b, &cc2);
+                te[4 * s] = (T)ki;
+                te[4 * s + 1] = (T)b;
+                te[4 * s + 2] = (T)cc2;
+                pml_point(d, c->dt, p.cpl[a], p.cph[a], n[a], l + 0.5, &ki, &b, &cc2);
+                th[4 * s] = (T)ki;
+                th[4 * s + 1] = (T)b;
+                th[4 * s + 2] = (T)cc2;
+            }
+            T* de = talloc(te.size());
+            T* dh = talloc(th.size());
+            CK(cudaMemcpy(de, te.data(), te.size() * sizeof(T), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(dh, th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
+            p.pmlE[a] = de;
+            p.pmlH[a] = dh;
+        }
+        p.inv_dx = (T)(1.0 / d.dx);
+        p.ch = (T)(c->dt / kMu0);
+        rho = talloc(c->nd);
+        p.rho = rho;
+        poles = (PoleTable<T>*)c->alloc(sizeof(PoleTable<T>));
+        CK(cudaMemset(poles, 0, sizeof(PoleTable<T>)));
+        p.poles = poles;
+        int pmax = 0;
+        for (int k = 0; k < 3; ++k) {
+            ptot[k] = p_total[k];
+            pmax = std::max(pmax, ptot[k]);
+            p.Q[k] = (cpx<T>*)c->alloc(c->nd * std::max(ptot[k], 1) * sizeof(cpx<T>));
+        }
+        bucket = fdtd::pole_bucket(pmax);
+        for (int m = 0; m < 2; ++m) dft[m] = (double2*)c->alloc(c->nd * 3 * d.n_freq * sizeof(double2));
+        // phase table (cos, sin)(w_f n dt), n = 0..M, evaluated in FP64 and stored in T
+        {
+            std::vector<V2> ph((size_t)(d.n_steps + 1) * d.n_freq);
+            for (int s = 0; s <= d.n_steps; ++s)
+                for (int f = 0; f < d.n_freq; ++f) {
+                    const double arg = 2.0 * kPi * c->freqs[f] * c->dt * (double)s;
+                    V2 v;
+                    v.x = (T)std::cos(arg);
+                    v.y = (T)std::sin(arg);
+                    ph[(size_t)s * d.n_freq + f] = v;
+                }
+            phase = (V2*)c->alloc(ph.size() * sizeof(V2));
+            CK(cudaMemcpy(phase, ph.data(), ph.size() * sizeof(V2), cudaMemcpyHostToDevice));
+        }
+        p.K = fdtd::kMaxSnap;
+        snap = talloc((size_t)fdtd::kMaxSnap * 3 * c->nd);
+        p.snap = snap;
+        staging = c->alloc(std::max<size_t>(c->nd, 1) * sizeof(double));
+        for (int m = 0; m < 2; ++m) {
+            dp[m].nd = (long long)c->nd;
+            dp[m].nf = d.n_freq;
+            dp[m].K = fdtd::kMaxSnap;
+            dp[m].snap = snap;
+            dp[m].dft = dft[m];
+            dp[m].ph = phase;
+        }
+        ctl = (int*)c->alloc(4 * sizeof(int));
+        CK(cudaMemset(ctl, 0, 4 * sizeof(int)));
+        p.ctl = ctl;
+        for (int m = 0; m < 2; ++m) dp[m].ctl = ctl;
+        p.nblocks_e = fdtd::e_blocks(d.nx, d.ny, d.nz);
+        p.blowup = (T)1e30;
+        p.tfsf_i0 = -1;
+        p.nb = 0;
+        std::fill(p.sb, p.sb + 6, 0);
+        einc = talloc(d.n_steps);
+        hinc = talloc(d.n_steps);
+        CK(cudaMemset(einc, 0, d.n_steps * sizeof(T)));
+        CK(cudaMemset(hinc, 0, d.n_steps * sizeof(T)));
+        p.einc = einc;
+        p.hinc = hinc;
+        // point-source tables: forward (1 basis, 1 voxel box), adjoint (2F bases, gap box)
+        src_wave[0] = talloc(d.n_steps);
+        src_r[0] = talloc(3);
+        src_wave[1] = talloc((size_t)d.n_steps * 2 * d.n_freq);
+        src_r[1] = talloc(std::max<size_t>(c->ngap * 3 * 2 * d.n_freq, 1));
+        gapbuf = (double2*)c->alloc(std::max<size_t>(c->ngap * 3 * d.n_freq, 1) * sizeof(double2));
+        grad = (double*)c->alloc(std::max<size_t>(c->nd, 1) * sizeof(double));
+        const size_t nblk = (c->nd + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads;
+        partial = (double*)c->alloc((nblk + 1) * sizeof(double));
+        counter = (unsigned*)c->alloc(sizeof(unsigned));
+        CK(cudaMemset(counter, 0, sizeof(unsigned)));
+        AB = (double2*)c->alloc(3 * d.n_freq * 2 * sizeof(double2));
+        pf = base;
+        pa = base;
+        build_forward_source();
+    }
+
+    void build_forward_source()
+    {
+        const fdtd_grid_desc& d = c->d;
+        if (d.src_kind == 0) {
+            std::vector<T> w(d.n_steps), r(3, T(0));
+            for (int s = 0; s < d.n_steps; ++s) w[s] = (T)src_pulse(d, (s + 0.5) * c->dt);
+            r[d.src_comp] = (T)(d.src_amp * kEps0 / c->dt);
+            CK(cudaMemcpy(src_wave[0], w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(src_r[0], r.data(), 3 * sizeof(T), cudaMemcpyHostToDevice));
+            pf.nb = 1;
+            pf.src_r = src_r[0];
+            pf.src_wave = src_wave[0];
+            const int sb[6] = {d.src_pos[0], d.src_pos[0] + 1, d.src_pos[1], d.src_pos[1] + 1, d.src_pos[2], d.src_pos[2] + 1};
+            std::memcpy(pf.sb, sb, sizeof sb);
+            pf.tfsf_i0 = -1;
+        } else {
+            pf.nb = 0;
+            pf.tfsf_i0 = d.src_pos[0];
+        }
+    }
+
+    // Incident plane wave of the one-sided TF/SF source: a 1-D Yee line along x with the grid's
+    // dx and dt in the background's z-component medium, hard-driven at its first node; node 2
+    // maps onto the first total-field plane.  Long enough that its far end never echoes back.
+    void build_incident(const Material& bg)
+    {
+        const fdtd_grid_desc& d = c->d;
+        if (d.src_kind != 1) return;
+        const int M = d.n_steps, off = 2;
+        const int L = off + (int)std::ceil(0.6 * M) + 16;
+        std::vector<double> e(L, 0.0), h(L, 0.0);
+        std::vector<T> ei(M), hi(M);
+        const double dt = c->dt, dx = d.dx;
+        const double Dp = kEps0 * bg.eps[2] / dt + 0.5 * bg.sig[2];
+        const double Dm = kEps0 * bg.eps[2] / dt - 0.5 * bg.sig[2];
+        const double chx = dt / (kMu0 * dx);
+        e[0] = d.src_amp * src_pulse(d, 0.0);
+        for (int s = 0; s < M; ++s) {
+            ei[s] = (T)e[off];
+            for (int m = 0; m + 1 < L; ++m) h[m] += chx * (e[m + 1] - e[m]);
+            h[L - 1] += chx * (0.0 - e[L - 1]);
+            hi[s] = (T)h[off - 1];
+            for (int m = 1; m < L; ++m) e[m] = (Dm * e[m] + (h[m] - h[m - 1]) / dx) / Dp;
+            e[0] = d.src_amp * src_pulse(d, (s + 1) * dt);
+        }
+        CK(cudaMemcpy(einc, ei.data(), M * sizeof(T), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(hinc, hi.data(), M * sizeof(T), cudaMemcpyHostToDevice));
+    }
+
+    void set_materials(const Material& bg, const Material& m1, const Material& m2, double gamma)
+    {
+        const double dt = c->dt;
+        PoleTable<T> tab;
+        std::memset(&tab, 0, sizeof tab);
+        std::vector<double2> ab(3 * c->d.n_freq * 2);
+        for (int k = 0; k < 3; ++k) {
+            const int P1 = (int)m1.poles[k].size(), P2 = (int)m2.poles[k].size();
+            if (P1 + P2 != ptot[k]) arg_error("pole counts differ from those the handle was created with");
+            // background
+            {
+                const double Dp = kEps0 * bg.eps[k] / dt + 0.5 * bg.sig[k];
+                const double Dm = kEps0 * bg.eps[k] / dt - 0.5 * bg.sig[k];
+                if (!(Dp > 0.0)) arg_error("background update denominator <= 0");
+                base.bg_ca[k] = (T)(Dm / Dp);
+                base.bg_cb[k] = (T)(1.0 / Dp);
+            }
+            double D[2], N[2];
+            const Material* mm[2] = {&m1, &m2};
+            for (int i = 0; i < 2; ++i) {
+                double sb = 0.0;
+                for (const Pole& q : mm[i]->poles[k]) {
+                    const cd am1 = expm1c(q.a * dt);
+                    sb += (kEps0 * q.c * am1 / (2.0 * q.a)).real();
+                }
+                D[i] = kEps0 * mm[i]->eps[k] / dt + 0.5 * mm[i]->sig[k] + 2.0 * sb / dt;
+                N[i] = kEps0 * mm[i]->eps[k] / dt - 0.5 * mm[i]->sig[k] - 2.0 * sb / dt;
+                if (!(D[i] > 0.0)) arg_error("material update denominator <= 0 (eps_inf too small for these poles)");
+            }
+            base.D1[k] = (T)D[0];
+            base.dD[k] = (T)(D[1] - D[0]);
+            base.N1[k] = (T)N[0];
+            base.dN[k] = (T)(N[1] - N[0]);
+            base.P[k] = P1 + P2;
+            base.P1[k] = P1;
+            std::vector<cd> alpha(P1 + P2), beta(P1 + P2), am1v(P1 + P2);
+            for (int p = 0; p < P1 + P2; ++p) {
+                const Pole& q = p < P1 ? m1.poles[k][p] : m2.poles[k][p - P1];
+                const cd am1 = expm1c(q.a * dt);
+                const cd be = kEps0 * q.c * am1 / (2.0 * q.a);
+                am1v[p] = am1;
+                alpha[p] = 1.0 + am1;
+                beta[p] = be;
+                tab.am1[k][p] = cpx<T>{(T)am1.real(), (T)am1.imag()};
+                tab.beta[k][p] = cpx<T>{(T)be.real(), (T)be.imag()};
+                const cd g = 2.0 / dt * am1;
+                tab.g[k][p] = cpx<T>{(T)g.real(), (T)g.imag()};
+            }
+            // gradient constants: dY/drho = A + (1 - 2 rho) B at each objective frequency
+            for (int f = 0; f < c->d.n_freq; ++f) {
+                const double wdt = 2.0 * kPi * c->freqs[f] * dt;
+                const double s = std::sin(0.5 * wdt);
+                const cd zm1(-2.0 * s * s, std::sin(wdt));    // z - 1
+                const cd zp1 = zm1 + 2.0;                       // z + 1
+                cd poles_sum = 0.0;
+                for (int p = 0; p < P1 + P2; ++p) {
+                    const cd h = beta[p] * zp1 / (zm1 - am1v[p]) + std::conj(beta[p]) * zp1 / (zm1 - std::conj(am1v[p]));
+                    poles_sum += (p < P1) ? -h : h;
+                }
+                const cd A = (kEps0 * (m2.eps[k] - m1.eps[k]) * zm1 + (m2.sig[k] - m1.sig[k]) * dt * zp1 / 2.0 + zm1 * poles_sum) / dt;
+                const cd B = gamma * zp1 / 2.0;
+                ab[(k * c->d.n_freq + f) * 2] = make_double2(A.real(), A.imag());
+                ab[(k * c->d.n_freq + f) * 2 + 1] = make_double2(B.real(), B.imag());
+            }
+        }
+        if (!(gamma >= 0.0)) arg_error("gamma must be >= 0");
+        base.hg = (T)(0.5 * gamma);
+        CK(cudaMemcpy(poles, &tab, sizeof tab, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(AB, ab.data(), ab.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        build_incident(bg);
+        refresh_params();
+    }
+
+    // Copy the material part of `base` into the forward / adjoint parameter sets.
+    void refresh_params()
+    {
+        KParams<T> f = base, a = base;
+        f.nb = pf.nb;
+        f.src_r = pf.src_r;
+        f.src_wave = pf.src_wave;
+        std::memcpy(f.sb, pf.sb, sizeof f.sb);
+        f.tfsf_i0 = pf.tfsf_i0;
+        a.nb = pa.nb;
+        a.src_r = pa.src_r;
+        a.src_wave = pa.src_wave;
+        std::memcpy(a.sb, pa.sb, sizeof a.sb);
+        a.tfsf_i0 = -1;
+        pf = f;
+        pa = a;
+        drop_graphs();
+    }
+
+    void drop_graphs()
+    {
+        for (auto& g : graph)
+            for (auto& x : g)
+                if (x) {
+                    cudaGraphExecDestroy(x);
+                    x = nullptr;
+                }
+    }
+
+    void set_density(const void* src, int dtype, int on_device)
+    {
+        const size_t n = c->nd;
+        int* flag = ctl + 2;
+        CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), c->work));
+        const void* dsrc = src;
+        if (!on_device) {   // host (pageable or pinned) -> staging, checked and converted on the device
+            CK(cudaMemcpyAsync(staging, src, n * (dtype == 0 ? 4 : 8), cudaMemcpyHostToDevice, c->work));
+            dsrc = staging;
+        }
+        CK(fdtd::launch_rho_import<T>(dsrc, dtype, (long long)n, rho, flag, c->work));
+        c->tim.launches++;
+        int hflag[4];
+        CK(cudaMemcpyAsync(hflag, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        if (hflag[2] & 2) arg_error("density value out of [0, 1] or non-finite");
+    }
+
+    void reset_state(int mode)
+    {
+        cudaStream_t s = c->work;
+        for (int k = 0; k < 3; ++k) {
+            CK(cudaMemsetAsync(base.E[k], 0, c->ncell * sizeof(T), s));
+            CK(cudaMemsetAsync(base.H[k], 0, c->ncell * sizeof(T), s));
+            for (int t = 0; t < 2; ++t) {
+                const int a = (k + 1 + t) % 3;
+                const int n[3] = {c->d.nx, c->d.ny, c->d.nz};
+                const size_t m = (size_t)(c->ncell / n[a]) * base.W[a];
+                if (m) {
+                    CK(cudaMemsetAsync(base.psiE[k][t], 0, m * sizeof(T), s));
+                    CK(cudaMemsetAsync(base.psiH[k][t], 0, m * sizeof(T), s));
+                }
+            }
+            if (ptot[k] && c->nd) CK(cudaMemsetAsync(base.Q[k], 0, c->nd * ptot[k] * sizeof(cpx<T>), s));
+        }
+        if (c->nd) CK(cudaMemsetAsync(dft[mode], 0, c->nd * 3 * c->d.n_freq * sizeof(double2), s));
+        CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), s));
+    }
+
+    void capture(int mode, int which, int steps)
+    {
+        const KParams<T>& p = mode ? pa : pf;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
+        cudaError_t err = cudaSuccess;
+        for (int s = 0; s < steps && err == cudaSuccess; ++s) {
+            err = fdtd::launch_h<T>(p, c->work);
+            if (err == cudaSuccess) err = fdtd::launch_e<T>(p, bucket, c->work);
+        }
+        if (err == cudaSuccess) err = fdtd::launch_dft<T>(dp[mode], steps, c->work);
+        cudaError_t e2 = cudaStreamEndCapture(c->work, &g);
+        if (err != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            throw Err{FDTD_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(err != cudaSuccess ? err : e2)};
+        }
+        cudaGraphExec_t ex = nullptr;
+        err = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        CK(err);
+        graph[mode][which] = ex;
+    }
+
+    void run(int mode)
+    {
+        const int M = c->d.n_steps;
+        reset_state(mode);
+        const KParams<T>& p = mode ? pa : pf;
+        const int K = std::min(M, kGraphSteps);
+        const int nblk = (M + K - 1) / K;
+        if (c->prof) {
+            // events: per step (before H, between H and E, after E), per block one after the DFT
+            const size_t need = 3 * (size_t)M + nblk;
+            while (c->ev.size() < need) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                c->ev.push_back(e);
+            }
+            int s = 0;
+            for (int b = 0; b < nblk; ++b) {
+                const int cnt = std::min(K, M - b * K);
+                for (int q = 0; q < cnt; ++q, ++s) {
+                    CK(cudaEventRecord(c->ev[3 * s], c->work));
+                    CK(fdtd::launch_h<T>(p, c->work));
+                    CK(cudaEventRecord(c->ev[3 * s + 1], c->work));
+                    CK(fdtd::launch_e<T>(p, bucket, c->work));
+                    CK(cudaEventRecord(c->ev[3 * s + 2], c->work));
+                }
+                CK(fdtd::launch_dft<T>(dp[mode], cnt, c->work));
+                CK(cudaEventRecord(c->ev[3 * (size_t)M + b], c->work));
+                if ((s % kChunkSteps) < K && c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
+            }
+            CK(cudaStreamSynchronize(c->work));
+            for (int q = 0; q < M; ++q) {
+                float a = 0, b = 0;
+                CK(cudaEventElapsedTime(&a, c->ev[3 * q], c->ev[3 * q + 1]));
+                CK(cudaEventElapsedTime(&b, c->ev[3 * q + 1], c->ev[3 * q + 2]));
+                c->tim.h_ms += a;
+                c->tim.e_ms += b;
+            }
+            for (int b = 0; b < nblk; ++b) {
+                const int last = std::min(M, (b + 1) * K) - 1;
+                float a = 0;
+                CK(cudaEventElapsedTime(&a, c->ev[3 * last + 2], c->ev[3 * (size_t)M + b]));
+                c->tim.dft_ms += a;
+            }
+        } else {
+            const int full = M / K, rem = M % K;
+            if (!graph[mode][0]) capture(mode, 0, K);
+            if (rem && !graph[mode][1]) capture(mode, 1, rem);
+            for (int r = 0; r < full; ++r) {
+                CK(cudaGraphLaunch(graph[mode][0], c->work));
+                if (((r + 1) * K) % kChunkSteps < K && c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
+            }
+            if (rem) CK(cudaGraphLaunch(graph[mode][1], c->work));
+        }
+        c->tim.h_launches += M;
+        c->tim.e_launches += M;
+        if (c->nd) {
+            c->tim.dft_launches += nblk;
+            c->tim.launches += nblk;
+        }
+        c->tim.launches += 2LL * M;
+        int hctl[4];
+        CK(cudaMemcpyAsync(hctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        if (hctl[2] & 1) {
+            c->dead = true;
+            throw Err{FDTD_ERR_UNSTABLE, "non-finite or exploding field during the run"};
+        }
+        if (hctl[0] != M) throw Err{FDTD_ERR_CUDA, "device step counter " + std::to_string(hctl[0]) + " != " + std::to_string(M)};
+    }
+
+    double forward(double* gap_out)
+    {
+        run(0);
+        const fdtd_grid_desc& d = c->d;
+        const size_t ns = c->ngap * 3 * d.n_freq;
+        gap_dft.assign(2 * ns, 0.0);
+        double F = 0.0;
+        if (ns) {
+            CK(fdtd::launch_gap_gather(dft[0], (long long)c->nd, d.n_freq, base.db, base.dnx, base.dny, base.gb, gapbuf, c->work));
+            c->tim.launches++;
+            CK(cudaMemcpyAsync(gap_dft.data(), gapbuf, ns * sizeof(double2), cudaMemcpyDeviceToHost, c->work));
+            CK(cudaStreamSynchronize(c->work));
+            for (int f = 0; f < d.n_freq; ++f) {
+                double s = 0.0;
+                for (size_t q = 0; q < 3 * c->ngap; ++q) {
+                    const double re = gap_dft[2 * (f * 3 * c->ngap + q)], im = gap_dft[2 * (f * 3 * c->ngap + q) + 1];
+                    s += re * re + im * im;
+                }
+                F += c->weights[f] * s;
+            }
+        }
+        if (gap_out && ns) std::memcpy(gap_out, gap_dft.data(), 2 * ns * sizeof(double));
+        return F;
+    }
+
+    // Adjoint drive: 2F basis pulses b_q(t) = g(t) {cos, sin}(w_f (t - t0a)) and, per gap sample,
+    // the real coefficients r_g with sum_q r_{g,q} Bhat_q(w_f) = w_f conj(Ehat_g(w_f)).
+    void adjoint()
+    {
+        const fdtd_grid_desc& d = c->d;
+        const int F = d.n_freq, nb = 2 * F, M = d.n_steps;
+        if (!c->ngap) arg_error("the adjoint run needs a non-empty gap box");
+        const double tau = d.adj_tau > 0.0 ? d.adj_tau : src_tau(d);
+        const double t0 = 4.0 * tau;
+        std::vector<double> wave((size_t)M * nb);
+        for (int s = 0; s < M; ++s) {
+            const double x = (s + 0.5) * c->dt - t0;
+            const double env = std::exp(-x * x / (2.0 * tau * tau));
+            for (int f = 0; f < F; ++f) {
+                const double w = 2.0 * kPi * c->freqs[f];
+                wave[(size_t)s * nb + 2 * f] = env * std::cos(w * x);
+                wave[(size_t)s * nb + 2 * f + 1] = env * std::sin(w * x);
+            }
+        }
+        // A[row][q]: rows (Re f, Im f) of sum_n b_q((n+1/2)dt) e^{-j w_f n dt}
+        std::vector<double> A((size_t)nb * nb, 0.0);
+        for (int f = 0; f < F; ++f) {
+            const double w = 2.0 * kPi * c->freqs[f] * c->dt;
+            for (int s = 0; s < M; ++s) {
+                const double cr = std::cos(w * s), ci = -std::sin(w * s);
+                for (int q = 0; q < nb; ++q) {
+                    const double b = wave[(size_t)s * nb + q];
+                    A[(2 * f) * nb + q] += b * cr;
+                    A[(2 * f + 1) * nb + q] += b * ci;
+                }
+            }
+        }
+        double anorm = 0.0;                 // 1-norm, for the condition estimate below
+        for (int q = 0; q < nb; ++q) {
+            double col = 0.0;
+            for (int r0 = 0; r0 < nb; ++r0) col += std::fabs(A[r0 * nb + q]);
+            anorm = std::max(anorm, col);
+        }
+        // LU with partial pivoting, reused for every gap sample
+        std::vector<int> piv(nb);
+        for (int col = 0; col < nb; ++col) {
+            int pr = col;
+            for (int r = col + 1; r < nb; ++r)
+                if (std::fabs(A[r * nb + col]) > std::fabs(A[pr * nb + col])) pr = r;
+            if (A[pr * nb + col] == 0.0) arg_error("adjoint basis matrix is singular (try another adj_tau)");
+            piv[col] = pr;
+            if (pr != col)
+                for (int q = 0; q < nb; ++q) std::swap(A[col * nb + q], A[pr * nb + q]);
+            for (int r = col + 1; r < nb; ++r) {
+                A[r * nb + col] /= A[col * nb + col];
+                for (int q = col + 1; q < nb; ++q) A[r * nb + q] -= A[r * nb + col] * A[col * nb + q];
+            }
+        }
+        auto lu_solve = [&](std::vector<double>& x) {
+            for (int col = 0; col < nb; ++col) std::swap(x[col], x[piv[col]]);
+            for (int row = 0; row < nb; ++row)
+                for (int q = 0; q < row; ++q) x[row] -= A[row * nb + q] * x[q];
+            for (int row = nb - 1; row >= 0; --row) {
+                for (int q = row + 1; q < nb; ++q) x[row] -= A[row * nb + q] * x[q];
+                x[row] /= A[row * nb + row];
+            }
+        };
+        // cond_1 = |A|_1 |A^{-1}|_1; an ill-conditioned basis loses the adjoint drive's accuracy
+        {
+            double inorm = 0.0;
+            std::vector<double> e(nb);
+            std::vector<double> colsum(nb, 0.0);
+            for (int q = 0; q < nb; ++q) {
+                std::fill(e.begin(), e.end(), 0.0);
+                e[q] = 1.0;
+                lu_solve(e);
+                double cs = 0.0;
+                for (int r0 = 0; r0 < nb; ++r0) cs += std::fabs(e[r0]);
+                inorm = std::max(inorm, cs);
+            }
+            adj_cond = anorm * inorm;
+            const double limit = sizeof(T) == 4 ? 1e4 : 1e10;
+            if (!(adj_cond <= limit))
+                arg_error("adjoint basis too ill-conditioned for this precision (cond " + std::to_string(adj_cond) +
+                          "): lengthen n_steps, raise adj_tau, or spread the objective frequencies");
+        }
+        const size_t ns = c->ngap * 3;
+        std::vector<T> r(ns * nb);
+        std::vector<double> rhs(nb);
+        for (int cc = 0; cc < 3; ++cc)
+            for (size_t gv = 0; gv < c->ngap; ++gv) {
+                for (int f = 0; f < F; ++f) {
+                    const size_t o = 2 * ((size_t)(f * 3 + cc) * c->ngap + gv);
+                    rhs[2 * f] = c->weights[f] * gap_dft[o];
+                    rhs[2 * f + 1] = -c->weights[f] * gap_dft[o + 1];
+                }
+                lu_solve(rhs);
+                for (int q = 0; q < nb; ++q) r[(gv * 3 + cc) * nb + q] = (T)rhs[q];
+            }
+        std::vector<T> wt(wave.size());
+        for (size_t q = 0; q < wave.size(); ++q) wt[q] = (T)wave[q];
+        CK(cudaMemcpyAsync(src_wave[1], wt.data(), wt.size() * sizeof(T), cudaMemcpyHostToDevice, c->work));
+        CK(cudaMemcpyAsync(src_r[1], r.data(), r.size() * sizeof(T), cudaMemcpyHostToDevice, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        if (pa.nb != nb || pa.src_r != src_r[1]) {
+            pa.nb = nb;
+            pa.src_r = src_r[1];
+            pa.src_wave = src_wave[1];
+            std::memcpy(pa.sb, base.gb, sizeof pa.sb);
+            refresh_params();
+        }
+        run(1);
+    }
+
+    void gradient(void* out, int dtype, int on_device)
+    {
+        const size_t nd = c->nd;
+        GParams<T> g{};
+        std::memcpy(g.db, base.db, sizeof g.db);
+        std::memcpy(g.gb, base.gb, sizeof g.gb);
+        g.dnx = base.dnx;
+        g.dny = base.dny;
+        g.nd = (long long)nd;
+        g.nf = c->d.n_freq;
+        g.dft_f = dft[0];
+        g.dft_a = dft[1];
+        g.AB = AB;
+        g.rho = rho;
+        g.grad64 = grad;
+        g.grad32 = nullptr;
+        float* grad32_dev = (float*)staging;
+        if (on_device && out) {
+            if (dtype == 1) g.grad64 = (double*)out;
+            else g.grad32 = (float*)out;
+        } else if (out && dtype == 0) {
+            g.grad32 = grad32_dev;
+        }
+        g.partial = partial;
+        g.counter = counter;
+        const unsigned nblk = (unsigned)((nd + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads);
+        if (nblk == 0) return;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->prof) {
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, c->work));
+        }
+        CK(fdtd::launch_grad<T>(g, nblk, c->work));
+        c->tim.launches++;
+        c->tim.grad_launches++;
+        if (c->prof) {
+            CK(cudaEventRecord(e1, c->work));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            c->tim.grad_ms += ms;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        if (out && !on_device) {   // straight into the caller's (pageable or pinned) buffer
+            if (dtype == 1)
+                CK(cudaMemcpyAsync(out, grad, nd * sizeof(double), cudaMemcpyDeviceToHost, c->work));
+            else
+                CK(cudaMemcpyAsync(out, grad32_dev, nd * sizeof(float), cudaMemcpyDeviceToHost, c->work));
+            CK(cudaStreamSynchronize(c->work));
+        }
+    }
+
+    double grad_norm2()
+    {
+        const unsigned nblk = (unsigned)((c->nd + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads);
+        double v = 0.0;
+        CK(cudaMemcpyAsync(&v, partial + nblk, sizeof(double), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        return v;
+    }
+
+    void get_field(int which, double* dst)
+    {
+        T* src = which < 3 ? base.E[which] : base.H[which - 3];
+        std::vector<T> h(c->ncell);
+        CK(cudaMemcpyAsync(h.data(), src, c->ncell * sizeof(T), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        for (size_t q = 0; q < c->ncell; ++q) dst[q] = (double)h[q];
+    }
+
+    void get_dft(int adjoint, double* dst)
+    {
+        CK(cudaMemcpyAsync(dst, dft[adjoint ? 1 : 0], c->nd * 3 * c->d.n_freq * sizeof(double2), cudaMemcpyDeviceToHost,
+                           c->work));
+        CK(cudaStreamSynchronize(c->work));
+    }
+
+    void index_map(int which, int32_t* dst, size_t n)
+    {
+        int32_t* dev = nullptr;
+        CK(cudaMalloc(&dev, n * sizeof(int32_t)));
+        cudaError_t e = fdtd::launch_index_map<T>(pf, which, dev, c->work);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, dev, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->work);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
+        cudaFree(dev);
+        c->tim.launches++;
+        CK(e);
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+template <typename F>
+fdtd_status guarded(fdtd_ctx* c, F&& fn)
+{
+    try {
+        fn();
+        return FDTD_OK;
+    } catch (const Err& e) {
+        if (c) {
+            c->err = e.msg;
+            if (e.code == FDTD_ERR_CUDA) c->dead = true;
+        }
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host allocation failed";
+        return FDTD_ERR_OOM;
+    } catch (...) {
+        if (c) c->err = "unexpected exception";
+        return FDTD_ERR_CUDA;
+    }
+}
+
+template <typename T>
+Solver<T>* as(fdtd_ctx* c) { return static_cast<Solver<T>*>(c->impl.get()); }
+
+// Dispatch on the handle's precision.
+template <typename F>
+void dispatch(fdtd_ctx* c, F&& fn)
+{
+    if (c->d.precision == 64)
+        fn(as<double>(c));
+    else
+        fn(as<float>(c));
+}
+
+void enter(fdtd_ctx* c)
+{
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventRecord(c->fence, c->user));
+    CK(cudaStreamWaitEvent(c->work, c->fence, 0));
+}
+
+void leave(fdtd_ctx* c)
+{
+    CK(cudaEventRecord(c->fence, c->work));
+    CK(cudaStreamWaitEvent(c->user, c->fence, 0));
+}
+
+fdtd_status check_handle(fdtd_handle h, bool allow_dead = false)
+{
+    if (!h) return FDTD_ERR_ARG;
+    if (h->dead && !allow_dead) return FDTD_ERR_STATE;
+    return FDTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fdtd_status fdtd_footprint_bytes(const fdtd_grid_desc* desc, const int p_total[3], size_t* bytes)
+{
+    if (!desc || !p_total || !bytes) return FDTD_ERR_ARG;
+    return guarded(nullptr, [&] {
+        validate(*desc);
+        *bytes = footprint(*desc, p_total);
+    });
+}
+
+fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd_handle* out)
+{
+    if (!desc || !out) return FDTD_ERR_ARG;
+    *out = nullptr;
+    fdtd_ctx* c = new (std::nothrow) fdtd_ctx();
+    if (!c) return FDTD_ERR_OOM;
+    fdtd_status st = guarded(c, [&] {
+        validate(*desc);
+        c->d = *desc;
+        c->freqs.assign(desc->freqs_hz, desc->freqs_hz + desc->n_freq);
+        c->weights.assign(desc->n_freq, 1.0);
+        if (desc->freq_weights) c->weights.assign(desc->freq_weights, desc->freq_weights + desc->n_freq);
+        c->d.freqs_hz = c->freqs.data();
+        c->d.freq_weights = c->weights.data();
+        CK(cudaGetDevice(&c->device));
+        c->user = (cudaStream_t)cuda_stream;
+        CK(cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->fence, cudaEventDisableTiming));
+        c->dt = desc->courant * desc->dx / kC0;
+        c->ncell = (size_t)desc->nx * desc->ny * desc->nz;
+        c->nd = (size_t)box_count(desc->design_box);
+        c->ngap = (size_t)box_count(desc->gap_box);
+        for (int a = 0; a < 3; ++a) {
+            c->dn[a] = c->nd ? desc->design_box[2 * a + 1] - desc->design_box[2 * a] : 0;
+            c->gn[a] = c->ngap ? desc->gap_box[2 * a + 1] - desc->gap_box[2 * a] : 0;
+        }
+    });
+    if (st != FDTD_OK) {
+        fdtd_destroy(c);
+        return st;
+    }
+    *out = c;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_materials(fdtd_handle h, const fdtd_ccpr_material* bg, const fdtd_ccpr_material* m1,
+                               const fdtd_ccpr_material* m2, double gamma)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    return guarded(h, [&] {
+        const Material B = import_material(bg, "bg"), A1 = import_material(m1, "m1"), A2 = import_material(m2, "m2");
+        for (int k = 0; k < 3; ++k)
+            if (!B.poles[k].empty()) arg_error("background material must be non-dispersive (no poles)");
+        int pt[3];
+        for (int k = 0; k < 3; ++k) {
+            pt[k] = (int)(A1.poles[k].size() + A2.poles[k].size());
+            if (pt[k] > fdtd::kMaxPoles) arg_error("more than 16 poles on one component (m1 + m2)");
+        }
+        CK(cudaSetDevice(h->device));
+        if (!h->impl) {
+            if (h->d.precision == 64) {
+                auto* s = new Solver<double>(h);
+                h->impl.reset(s);
+                s->allocate(pt);
+            } else {
+                auto* s = new Solver<float>(h);
+                h->impl.reset(s);
+                s->allocate(pt);
+            }
+        }
+        dispatch(h, [&](auto* s) { s->set_materials(B, A1, A2, gamma); });
+        h->has_mat = true;
+        h->has_fwd = h->has_adj = h->has_grad = false;
+    });
+}
+
+fdtd_status fdtd_set_density(fdtd_handle h, const void* rho, size_t n, int dtype, int on_device)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if (!h->has_mat) {
+        h->err = "set_materials first";
+        return FDTD_ERR_STATE;
+    }
+    if (n != h->nd || (dtype != 0 && dtype != 1) || (!rho && n)) {
+        h->err = "density size/dtype mismatch: expected " + std::to_string(h->nd) + " values";
+        return FDTD_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        enter(h);
+        if (n) dispatch(h, [&](auto* s) { s->set_density(rho, dtype, on_device); });
+        leave(h);
+        h->has_rho = true;
+        h->has_fwd = h->has_adj = h->has_grad = false;
+    });
+}
+
+fdtd_status fdtd_forward(fdtd_handle h, double* F_out, double* gap_dft_out)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if (!h->has_mat || (h->nd && !h->has_rho)) {
+        h->err = "set_materials and set_density first";
+        return FDTD_ERR_STATE;
+    }
+    h->cancel.store(0);
+    return guarded(h, [&] {
+        enter(h);
+        double F = 0.0;
+        dispatch(h, [&](auto* s) { F = s->forward(gap_dft_out); });
+        leave(h);
+        if (F_out) *F_out = F;
+        h->has_fwd = true;
+        h->has_adj = h->has_grad = false;
+    });
+}
+
+fdtd_status fdtd_adjoint(fdtd_handle h)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if (!h->has_fwd) {
+        h->err = "adjoint before forward";
+        return FDTD_ERR_STATE;
+    }
+    h->cancel.store(0);
+    return guarded(h, [&] {
+        enter(h);
+        dispatch(h, [&](auto* s) { s->adjoint(); });
+        leave(h);
+        h->has_adj = true;
+    });
+}
+
+fdtd_status fdtd_gradient(fdtd_handle h, void* grad, size_t n, int dtype, int on_device)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if (!h->has_adj) {
+        h->err = "gradient before adjoint";
+        return FDTD_ERR_STATE;
+    }
+    if ((grad && n != h->nd) || (dtype != 0 && dtype != 1)) {
+        h->err = "gradient buffer size/dtype mismatch";
+        return FDTD_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        enter(h);
+        dispatch(h, [&](auto* s) { s->gradient(grad, dtype, on_device); });
+        leave(h);
+        h->has_grad = true;
+    });
+}
+
+fdtd_status fdtd_gradient_norm(fdtd_handle h, double* out)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if (!h->has_grad || !out) return FDTD_ERR_STATE;
+    return guarded(h, [&] { dispatch(h, [&](auto* s) { *out = s->grad_norm2(); }); });
+}
+
+fdtd_status fdtd_get_field(fdtd_handle h, int which, double* dst, size_t n)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    if (!h->impl || which < 0 || which > 5 || n != h->ncell || !dst) return FDTD_ERR_ARG;
+    return guarded(h, [&] { dispatch(h, [&](auto* s) { s->get_field(which, dst); }); });
+}
+
+fdtd_status fdtd_get_dft(fdtd_handle h, int adjoint, double* dst, size_t n_doubles)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    if (!h->impl || !dst || n_doubles != 2 * h->nd * 3 * (size_t)h->d.n_freq) return FDTD_ERR_ARG;
+    return guarded(h, [&] { dispatch(h, [&](auto* s) { s->get_dft(adjoint, dst); }); });
+}
+
+fdtd_status fdtd_get_index_map(fdtd_handle h, int which, int32_t* dst, size_t n)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    if (!h->impl || !dst || which < 0 || which > 3) return FDTD_ERR_ARG;
+    if (n != (which <= 1 ? 3 * h->ncell : h->ncell)) return FDTD_ERR_ARG;
+    return guarded(h, [&] { dispatch(h, [&](auto* s) { s->index_map(which, dst, n); }); });
+}
+
+fdtd_status fdtd_set_profiling(fdtd_handle h, int on)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    h->prof = on != 0;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    if (!out) return FDTD_ERR_ARG;
+    fdtd_timings t = h->tim;
+    const double ts = h->d.precision == 64 ? 8.0 : 4.0;
+    // algorithmic bytes per launch: every state word read once and written once
+    double be = 9.0 * ts * (double)h->ncell;            // E r/w, H read
+    double bh = 9.0 * ts * (double)h->ncell;            // H r/w, E read
+    const int n[3] = {h->d.nx, h->d.ny, h->d.nz};
+    for (int a = 0; a < 3; ++a) {
+        const double w = (double)h->d.cpml[2 * a] + h->d.cpml[2 * a + 1];
+        const double slab = (double)(h->ncell / n[a]) * w;
+        be += 2.0 * 2.0 * ts * slab;                       // two psi_E r/w
+        bh += 2.0 * 2.0 * ts * slab;
+    }
+    if (h->impl) {
+        int P = 0;
+        if (h->d.precision == 64) {
+            for (int k = 0; k < 3; ++k) P += as<double>(h)->ptot[k];
+        } else {
+            for (int k = 0; k < 3; ++k) P += as<float>(h)->ptot[k];
+        }
+        const double nd = (double)h->nd, nod = (double)(h->nd - h->ngap);
+        be += nod * ts + nod * P * 2.0 * 2.0 * ts;          // rho read, Q r/w (design, non-gap)
+        be += nd * 3.0 * ts;                                // E snapshot write (design box)
+        const double K = std::min(h->d.n_steps, kGraphSteps);
+        t.dft_steps_per_launch = K;
+        t.bytes_dft_per_launch = nd * (K * 3.0 * ts + 3.0 * h->d.n_freq * 16.0 * 2.0);  // snapshots + FP64 acc r/w
+        t.bytes_grad_per_launch = nd * (2.0 * 3.0 * h->d.n_freq * 16.0 + ts + 8.0);     // both DFTs, rho, grad
+    }
+    t.bytes_e_per_launch = be;
+    t.bytes_h_per_launch = bh;
+    *out = t;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_reset_timings(fdtd_handle h)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    h->tim = fdtd_timings{};
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_get_info(fdtd_handle h, double* dt, size_t* n_design, size_t* n_gap, size_t* device_bytes)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    if (dt) *dt = h->dt;
+    if (n_design) *n_design = h->nd;
+    if (n_gap) *n_gap = h->ngap;
+    if (device_bytes) *device_bytes = h->bytes;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_cancel(fdtd_handle h)
+{
+    if (!h) return FDTD_ERR_ARG;
+    h->cancel.store(1);
+    return FDTD_OK;
+}
+
+const char* fdtd_last_error(fdtd_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+fdtd_status fdtd_destroy(fdtd_handle h)
+{
+    if (!h) return FDTD_ERR_ARG;
+    cudaSetDevice(h->device);
+    if (h->work) cudaStreamSynchronize(h->work);
+    h->impl.reset();
+    h->free_all();
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->fence) cudaEventDestroy(h->fence);
+    if (h->work) cudaStreamDestroy(h->work);
+    delete h;
+    return FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// Launch wrappers and helper kernels; explicit FP32 / FP64 instantiations.
+#include "fdtd_kernels.cuh"
+#include "fdtd_launch.h"
+
+namespace fdtd {
+
+__global__ void gap_gather_kernel(const double2* dft, long long nd, int nf, int d0, int d2, int d4, int dnx, int dny,
+                                  int g0, int g1, int g2, int g3, int g4, int g5, double2* out)
+{
+    const int gnx = g1 - g0, gny = g3 - g2, gnz = g5 - g4;
+    const long long ng = (long long)gnx * gny * gnz;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ng * 3 * nf) return;
+    const long long gv = t % ng;
+    const long long fc = t / ng;
+    const int i = g0 + (int)(gv % gnx), j = g2 + (int)((gv / gnx) % gny), k = g4 + (int)(gv / ((long long)gnx * gny));
+    const long long dv = ((long long)(k - d4) * dny + (j - d2)) * dnx + (i - d0);
+    out[t] = dft[fc * nd + dv];
+}
+
+// Density import: float / double source -> T, with a range / finiteness check (flag bit 1).
+template <typename T, typename S>
+__global__ void rho_import_kernel(const S* src, long long n, T* dst, int* flag)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const S r = src[v];
+    if (!(r >= S(0) && r <= S(1))) atomicOr(flag, 2);
+    dst[v] = (T)r;
+}
+
+template <typename T>
+__global__ void to_double_kernel(const T* src, long long n, double* dst)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) dst[v] = (double)src[v];
+}
+
+// Integer maps from the same index helpers the update kernels use.
+template <typename T>
+__global__ void index_map_kernel(const KParams<T> p, int which, int32_t* out)
+{
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= p.nx || j >= p.ny) return;
+    const long long id = ((long long)k * p.ny + j) * p.nx + i;
+    const bool in_d = in_box(p.db, i, j, k);
+    const bool in_g = in_d && in_box(p.gb, i, j, k);
+    if (which == 2) {
+        out[id] = in_d ? (int32_t)(((long long)(k - p.db[4]) * p.dny + (j - p.db[2])) * p.dnx + (i - p.db[0])) : -1;
+        return;
+    }
+    if (which == 3) {
+        out[id] = in_g ? (int32_t)(((long long)(k - p.gb[4]) * p.gny + (j - p.gb[2])) * p.gnx + (i - p.gb[0])) : -1;
+        return;
+    }
+    const int l[3] = {i, j, k};
+    const int sl[3] = {slab_index(i, p.cpl[0], p.cph[0], p.nx), slab_index(j, p.cpl[1], p.cph[1], p.ny),
+                       slab_index(k, p.cpl[2], p.cph[2], p.nz)};
+    for (int c = 0; c < 3; ++c) {
+        int32_t v = 0;
+        for (int t = 0; t < 2; ++t) {
+            const int a = (c + 1 + t) % 3;
+            const T* tab = (which == 0) ? p.pmlE[a] : p.pmlH[a];
+            if (sl[a] >= 0 && tab[4 * sl[a] + 2] != T(0)) v |= 1 << (3 + t);
+        }
+        if (which == 0) {
+            v |= in_d ? (in_g ? 2 : 1) : 0;
+            bool fixed = false;
+            for (int a = 0; a < 3; ++a)
+                if (a != c && l[a] == 0) fixed = true;
+            if (fixed) v |= 4;
+            if (p.nb > 0 && in_box(p.sb, i, j, k)) {
+                const long long lv = ((long long)(k - p.sb[4]) * (p.sb[3] - p.sb[2]) + (j - p.sb[2])) * (p.sb[1] - p.sb[0]) + (i - p.sb[0]);
+                if (p.src_r[(lv * 3 + c) * p.nb] != T(0)) v |= 32;
+            }
+        }
+        out[(long long)c * p.ncell + id] = v;
+    }
+}
+
+static dim3 grid3(int nx, int ny, int nz) { return dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY, nz); }
+
+template <typename T>
+cudaError_t launch_h(const KParams<T>& p, cudaStream_t s)
+{
+    h_kernel<T><<<grid3(p.nx, p.ny, p.nz), dim3(kBX, kBY), 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+int pole_bucket(int max_poles)
+{
+    return max_poles == 0 ? 0 : max_poles <= 4 ? 4 : max_poles <= 8 ? 8 : 16;
+}
+
+template <typename T>
+cudaError_t launch_e(const KParams<T>& p, int bucket, cudaStream_t s)
+{
+    const dim3 g = grid3(p.nx, p.ny, p.nz), b(kBX, kBY);
+    switch (bucket) {
+    case 0: e_kernel<T, 0><<<g, b, 0, s>>>(p); break;
+    case 4: e_kernel<T, 4><<<g, b, 0, s>>>(p); break;
+    case 8: e_kernel<T, 8><<<g, b, 0, s>>>(p); break;
+    default: e_kernel<T, 16><<<g, b, 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s)
+{
+    if (d.nd == 0 || cnt <= 0) return cudaSuccess;
+    dft_kernel<T><<<(unsigned)((d.nd + kReduceThreads - 1) / kReduceThreads), kReduceThreads, 0, s>>>(d, cnt);
+    return cudaGetLastError();
+}
+
+unsigned e_blocks(int nx, int ny, int nz)
+{
+    const dim3 g = grid3(nx, ny, nz);
+    return g.x * g.y * g.z;
+}
+
+template <typename T>
+cudaError_t launch_grad(const GParams<T>& g, unsigned nblocks, cudaStream_t s)
+{
+    grad_kernel<T><<<nblocks, kReduceThreads, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gap_gather(const double2* dft, long long nd, int nf, const int* db, int dnx, int dny, const int* gb,
+                              double2* out, cudaStream_t s)
+{
+    const long long ng = (long long)(gb[1] - gb[0]) * (gb[3] - gb[2]) * (gb[5] - gb[4]);
+    const long long nt = ng * 3 * nf;
+    if (nt == 0) return cudaSuccess;
+    gap_gather_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(dft, nd, nf, db[0], db[2], db[4], dnx, dny, gb[0], gb[1],
+                                                                   gb[2], gb[3], gb[4], gb[5], out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rho_import(const void* src, int dtype, long long n, T* dst, int* flag, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (dtype == 0)
+        rho_import_kernel<T, float><<<nb, 256, 0, s>>>((const float*)src, n, dst, flag);
+    else
+        rho_import_kernel<T, double><<<nb, 256, 0, s>>>((const double*)src, n, dst, flag);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_to_double(const T* src, long long n, double* dst, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    to_double_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaStream_t s)
+{
+    index_map_kernel<T><<<grid3(p.nx, p.ny, p.nz), dim3(kBX, kBY), 0, s>>>(p, which, out);
+    return cudaGetLastError();
+}
+
+#define FDTD_INSTANTIATE(T)                                                                              \
+    template cudaError_t launch_h<T>(const KParams<T>&, cudaStream_t);                                   \
+    template cudaError_t launch_e<T>(const KParams<T>&, int, cudaStream_t);                              \
+    template cudaError_t launch_dft<T>(const DParams<T>&, int, cudaStream_t);                            \
+    template cudaError_t launch_grad<T>(const GParams<T>&, unsigned, cudaStream_t);                      \
+    template cudaError_t launch_rho_import<T>(const void*, int, long long, T*, int*, cudaStream_t);      \
+    template cudaError_t launch_to_double<T>(const T*, long long, double*, cudaStream_t);                \
+    template cudaError_t launch_index_map<T>(const KParams<T>&, int, int32_t*, cudaStream_t);
+
+FDTD_INSTANTIATE(float)
+FDTD_INSTANTIATE(double)
+
+}  // namespace fdtd

@@ -1,0 +1,470 @@
+// Device kernels of the CCPR time-domain adjoint gradient (arXiv 2305.00234) for sm_103a.
+//
+// The time step is split into the two memory-bound stencil kernels of the Yee scheme:
+//   h_kernel: H^{n+1/2} = H^{n-1/2} - (dt/mu0) curl E^n                      (Eq. (Maxwells)c)
+//             with CFS-CPML psi only for cells inside the edge slabs;
+//   e_kernel: E^{n+1} from curl H^{n+1/2}, the conductivity and the CCPR pole currents of both
+//             materials weighted by 1-rho and rho (Eqs. (Maxwells)a,b, (eps_mixed),
+//             (sigma_mixed), (Poles_mixed)); the pole recursion
+//             Q <- Q + (alpha-1) Q + beta (E^{n+1}+E^n); the point / TF-SF sources; the running
+//             FP64 DFT of E over the design box, fused so E is not read twice.
+// and the per-voxel gradient kernel (structure of Eq. (Gradient_analytic)) with a deterministic
+// warp-shuffle reduction of its squared norm.
+//
+// Thread layout: block (32, 8) over (x, y), one z plane per blockIdx.z; x is the fastest array
+// axis, so each warp reads and writes 128 contiguous bytes per field (FP32).  Neighbour reads
+// at -1 (E kernel) / +1 (H kernel) come from L1/L2: the plane k-1 was touched by blocks
+// scheduled just before, so DRAM sees each array about once per kernel.
+//
+// The step index n lives in device memory (ctl[0]) so that a captured CUDA graph of K steps
+// can be replayed: both kernels read it, and the last E block to finish advances it.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+constexpr int kMaxPoles = 16;     // per component, m1 + m2
+constexpr int kMaxFreq = 8;
+constexpr int kMaxBasis = 2 * kMaxFreq;
+constexpr int kBX = 32;
+constexpr int kBY = 8;
+constexpr int kReduceThreads = 256;
+constexpr int kMaxSnap = 16;      // steps per blocked DFT update (snapshot ring length)
+
+template <typename T>
+struct cpx {
+    T re, im;
+};
+
+// Pole coefficients of one handle, in device memory (uniform loads through the read-only path).
+template <typename T>
+struct PoleTable {
+    cpx<T> am1[3][kMaxPoles];    // alpha - 1 = e^{a dt} - 1
+    cpx<T> beta[3][kMaxPoles];   // eps0 c (e^{a dt} - 1) / (2 a)
+    cpx<T> g[3][kMaxPoles];      // (2/dt)(alpha - 1): weight of Re{(alpha-1) Q} in the E update
+};
+
+template <typename T>
+struct KParams {
+    int nx, ny, nz;
+    long long plane, ncell;
+    int db[6], gb[6], sb[6];     // design, gap, point-source boxes (half-open)
+    int dnx, dny;
+    long long dplane, nd;
+    int gnx, gny;
+    long long gplane;
+    int cpl[3], cph[3], W[3];    // CPML thickness low / high, slab width per axis
+    T* E[3];
+    T* H[3];
+    T* psiE[3][2];               // component c, derivative axis (c+1+t)%3
+    T* psiH[3][2];
+    const T* pmlE[3];            // per axis, per slab index: {1/kappa, b, c, 0} at integer positions
+    const T* pmlH[3];            //                           ... at half-integer positions
+    T inv_dx, ch;                // 1/dx, dt/mu0
+    T bg_ca[3], bg_cb[3];        // background: E' = ca E + cb drive
+    T D1[3], dD[3], N1[3], dN[3], hg;   // design: D(rho) = D1 + rho dD + hg rho(1-rho), N likewise
+    int P[3], P1[3];             // poles per component (m1 first, P1 of them)
+    const PoleTable<T>* poles;
+    const T* rho;                // design box density
+    cpx<T>* Q[3];                // pole currents [P[c]][nd]
+    int K;                       // snapshot ring length (steps per DFT block)
+    T* snap;                     // E snapshots of the design box [K][3][nd]
+    int nb;                      // point-source basis functions (0 = none)
+    const T* src_r;              // [(local sample)*nb + q], local sample = local voxel*3 + c
+    const T* src_wave;           // [n*nb + q]
+    int tfsf_i0;                 // first total-field x index, -1 = no TF/SF
+    const T* einc;               // E_inc^n at x = i0 dx
+    const T* hinc;               // H_inc^{n+1/2} at x = (i0 - 1/2) dx
+    int* ctl;                    // [0] step n, [1] finished E blocks, [2] flags (bit 0: unstable)
+    unsigned nblocks_e;
+    T blowup;
+};
+
+__device__ __forceinline__ bool in_box(const int* b, int i, int j, int k)
+{
+    return i >= b[0] && i < b[1] && j >= b[2] && j < b[3] && k >= b[4] && k < b[5];
+}
+
+// Index inside the two CPML slabs [0, lo) and [n-hi, n) of one axis, -1 outside.
+__device__ __forceinline__ int slab_index(int l, int lo, int hi, int n)
+{
+    return l < lo ? l : (l >= n - hi ? lo + (l - (n - hi)) : -1);
+}
+
+template <typename T>
+__device__ __forceinline__ long long psi_index(const KParams<T>& p, int i, int j, int k, int a, int s)
+{
+    if (a == 0) return ((long long)k * p.ny + j) * p.W[0] + s;
+    if (a == 1) return ((long long)k * p.W[1] + s) * p.nx + i;
+    return ((long long)s * p.ny + j) * p.nx + i;
+}
+
+// CFS-CPML: psi <- b psi + c d ; derivative -> d / kappa + psi.
+template <typename T>
+__device__ __forceinline__ T stretch(T d, const T* __restrict__ tab, int s, T* psi)
+{
+    const T kinv = __ldg(tab + 4 * s), b = __ldg(tab + 4 * s + 1), c = __ldg(tab + 4 * s + 2);
+    const T v = b * (*psi) + c * d;
+    *psi = v;
+    return d * kinv + v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg_t(const T* p) { return __ldg(p); }
+
+template <typename T>
+__device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p)
+{
+    cpx<T> v;
+    v.re = __ldg(&p->re);
+    v.im = __ldg(&p->im);
+    return v;
+}
+
+// E update of one design sample (blended), with Q^n:
+//   E' = (N(rho) E + drive - sum_p kappa_p Re{g_p Q_p}) / D(rho),
+//   Q_p <- Q_p + (alpha_p - 1) Q_p + beta_p (E' + E).
+// MP bounds the poles per component at compile time so the pole currents stay in registers.
+template <typename T, int MP>
+__device__ __forceinline__ T design_sample(const KParams<T>& p, int c, T rho, long long dv, T e_old, T drive)
+{
+    const T one = T(1);
+    const T gm = p.hg * rho * (one - rho);
+    const T D = p.D1[c] + rho * p.dD[c] + gm;
+    const T N = p.N1[c] + rho * p.dN[c] - gm;
+    if (MP == 0) return (N * e_old + drive) / D;
+    const int P = p.P[c], P1 = p.P1[c];
+    cpx<T>* __restrict__ Q = p.Q[c];
+    const PoleTable<T>* __restrict__ tab = p.poles;
+    cpx<T> q[MP > 0 ? MP : 1];
+#pragma unroll
+    for (int pp = 0; pp < MP; ++pp)
+        if (pp < P) q[pp] = Q[pp * p.nd + dv];
+    T sq = T(0);
+#pragma unroll
+    for (int pp = 0; pp < MP; ++pp) {
+        if (pp < P) {
+            const T kap = pp < P1 ? one - rho : rho;
+            const cpx<T> g = ldg_c(&tab->g[c][pp]);
+            sq += kap * (g.re * q[pp].re - g.im * q[pp].im);
+        }
+    }
+    const T e_new = (N * e_old + drive - sq) / D;
+    const T es = e_new + e_old;
+#pragma unroll
+    for (int pp = 0; pp < MP; ++pp) {
+        if (pp < P) {
+            const cpx<T> a = ldg_c(&tab->am1[c][pp]);
+            const cpx<T> b = ldg_c(&tab->beta[c][pp]);
+            cpx<T> v;
+            v.re = q[pp].re + (a.re * q[pp].re - a.im * q[pp].im) + b.re * es;
+            v.im = q[pp].im + (a.re * q[pp].im + a.im * q[pp].re) + b.im * es;
+            Q[pp * p.nd + dv] = v;
+        }
+    }
+    return e_new;
+}
+
+template <typename T>
+__device__ __forceinline__ T point_drive(const KParams<T>& p, int i, int j, int k, int c, int n)
+{
+    const long long lv = ((long long)(k - p.sb[4]) * (p.sb[3] - p.sb[2]) + (j - p.sb[2])) * (p.sb[1] - p.sb[0]) + (i - p.sb[0]);
+    const T* r = p.src_r + (lv * 3 + c) * p.nb;
+    const T* w = p.src_wave + (long long)n * p.nb;
+    T s = T(0);
+    for (int q = 0; q < p.nb; ++q) s += __ldg(r + q) * __ldg(w + q);
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ int read_step(const int* ctl) { return __ldcg(ctl); }
+
+template <typename T>
+__global__ void __launch_bounds__(kBX * kBY) h_kernel(const KParams<T> p)
+{
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= p.nx || j >= p.ny) return;
+    const long long id = ((long long)k * p.ny + j) * p.nx + i;
+    const T* __restrict__ Ex = p.E[0];
+    const T* __restrict__ Ey = p.E[1];
+    const T* __restrict__ Ez = p.E[2];
+    T* __restrict__ Hx = p.H[0];
+    T* __restrict__ Hy = p.H[1];
+    T* __restrict__ Hz = p.H[2];
+    const bool ip = i + 1 < p.nx, jp = j + 1 < p.ny, kp = k + 1 < p.nz;
+    // every load first
+    const T ex = Ex[id], ey = Ey[id], ez = Ez[id];
+    const T ex_j = jp ? Ex[id + p.nx] : T(0), ex_k = kp ? Ex[id + p.plane] : T(0);
+    const T ey_i = ip ? Ey[id + 1] : T(0), ey_k = kp ? Ey[id + p.plane] : T(0);
+    const T ez_i = ip ? Ez[id + 1] : T(0), ez_j = jp ? Ez[id + p.nx] : T(0);
+    const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
+    const int sx = slab_index(i, p.cpl[0], p.cph[0], p.nx);
+    const int sy = slab_index(j, p.cpl[1], p.cph[1], p.ny);
+    const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
+    const T idx = p.inv_dx, ch = p.ch;
+    // H_x at (i, j+1/2, k+1/2): (curl E)_x = dEz/dy - dEy/dz
+    T xa = (ez_j - ez) * idx, xb = (ey_k - ey) * idx;
+    // H_y at (i+1/2, j, k+1/2): (curl E)_y = dEx/dz - dEz/dx
+    T ya = (ex_k - ex) * idx, yb = (ez_i - ez) * idx;
+    // H_z at (i+1/2, j+1/2, k): (curl E)_z = dEy/dx - dEx/dy
+    T za = (ey_i - ey) * idx, zb = (ex_j - ex) * idx;
+    if (i == p.tfsf_i0 - 1) yb -= __ldg(p.einc + read_step<T>(p.ctl)) * idx;   // H_y here is scattered field
+    if (sy >= 0) {
+        xa = stretch(xa, p.pmlH[1], sy, p.psiH[0][0] + psi_index(p, i, j, k, 1, sy));
+        zb = stretch(zb, p.pmlH[1], sy, p.psiH[2][1] + psi_index(p, i, j, k, 1, sy));
+    }
+    if (sz >= 0) {
+        xb = stretch(xb, p.pmlH[2], sz, p.psiH[0][1] + psi_index(p, i, j, k, 2, sz));
+        ya = stretch(ya, p.pmlH[2], sz, p.psiH[1][0] + psi_index(p, i, j, k, 2, sz));
+    }
+    if (sx >= 0) {
+        yb = stretch(yb, p.pmlH[0], sx, p.psiH[1][1] + psi_index(p, i, j, k, 0, sx));
+        za = stretch(za, p.pmlH[0], sx, p.psiH[2][0] + psi_index(p, i, j, k, 0, sx));
+    }
+    Hx[id] = hx - ch * (xa - xb);
+    Hy[id] = hy - ch * (ya - yb);
+    Hz[id] = hz - ch * (za - zb);
+}
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kBX * kBY) e_kernel(const KParams<T> p)
+{
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k = blockIdx.z;
+    const int n = read_step<T>(p.ctl);
+    if (i < p.nx && j < p.ny) {
+        const long long id = ((long long)k * p.ny + j) * p.nx + i;
+        const T* __restrict__ Hx = p.H[0];
+        const T* __restrict__ Hy = p.H[1];
+        const T* __restrict__ Hz = p.H[2];
+        T* __restrict__ Ex = p.E[0];
+        T* __restrict__ Ey = p.E[1];
+        T* __restrict__ Ez = p.E[2];
+        const bool im = i > 0, jm = j > 0, km = k > 0;
+        // every field load first
+        const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
+        const T hz_j = jm ? Hz[id - p.nx] : T(0), hy_k = km ? Hy[id - p.plane] : T(0);
+        const T hx_k = km ? Hx[id - p.plane] : T(0), hz_i = im ? Hz[id - 1] : T(0);
+        const T hy_i = im ? Hy[id - 1] : T(0), hx_j = jm ? Hx[id - p.nx] : T(0);
+        const T ex0 = Ex[id], ey0 = Ey[id], ez0 = Ez[id];
+        const int sx = slab_index(i, p.cpl[0], p.cph[0], p.nx);
+        const int sy = slab_index(j, p.cpl[1], p.cph[1], p.ny);
+        const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
+        const bool in_d = in_box(p.db, i, j, k);
+        const bool design = in_d && !in_box(p.gb, i, j, k);
+        const long long dv = in_d ? ((long long)(k - p.db[4]) * p.dny + (j - p.db[2])) * p.dnx + (i - p.db[0]) : 0;
+        const T rho = design ? p.rho[dv] : T(0);
+        const T idx = p.inv_dx;
+        // E_x at (i+1/2, j, k): dHz/dy - dHy/dz
+        T xa = (hz - hz_j) * idx, xb = (hy - hy_k) * idx;
+        // E_y at (i, j+1/2, k): dHx/dz - dHz/dx
+        T ya = (hx - hx_k) * idx, yb = (hz - hz_i) * idx;
+        // E_z at (i, j, k+1/2): dHy/dx - dHx/dy
+        T za = (hy - hy_i) * idx, zb = (hx - hx_j) * idx;
+        if (i == p.tfsf_i0) za -= __ldg(p.hinc + n) * idx;    // H_y(i0-1/2) is scattered field
+        if (sy >= 0) {
+            xa = stretch(xa, p.pmlE[1], sy, p.psiE[0][0] + psi_index(p, i, j, k, 1, sy));
+            zb = stretch(zb, p.pmlE[1], sy, p.psiE[2][1] + psi_index(p, i, j, k, 1, sy));
+        }
+        if (sz >= 0) {
+            xb = stretch(xb, p.pmlE[2], sz, p.psiE[0][1] + psi_index(p, i, j, k, 2, sz));
+            ya = stretch(ya, p.pmlE[2], sz, p.psiE[1][0] + psi_index(p, i, j, k, 2, sz));
+        }
+        if (sx >= 0) {
+            yb = stretch(yb, p.pmlE[0], sx, p.psiE[1][1] + psi_index(p, i, j, k, 0, sx));
+            za = stretch(za, p.pmlE[0], sx, p.psiE[2][0] + psi_index(p, i, j, k, 0, sx));
+        }
+        T dx_ = xa - xb, dy_ = ya - yb, dz_ = za - zb;
+        if (p.nb > 0 && in_box(p.sb, i, j, k)) {
+            dx_ += point_drive(p, i, j, k, 0, n);
+            dy_ += point_drive(p, i, j, k, 1, n);
+            dz_ += point_drive(p, i, j, k, 2, n);
+        }
+        T ex, ey, ez;
+        if (design) {
+            ex = design_sample<T, MP>(p, 0, rho, dv, ex0, dx_);
+            ey = design_sample<T, MP>(p, 1, rho, dv, ey0, dy_);
+            ez = design_sample<T, MP>(p, 2, rho, dv, ez0, dz_);
+        } else {
+            ex = p.bg_ca[0] * ex0 + p.bg_cb[0] * dx_;
+            ey = p.bg_ca[1] * ey0 + p.bg_cb[1] * dy_;
+            ez = p.bg_ca[2] * ez0 + p.bg_cb[2] * dz_;
+        }
+        // PEC walls: components tangential to a wall at index 0 stay zero
+        if (!(jm && km)) ex = ex0;
+        if (!(km && im)) ey = ey0;
+        if (!(im && jm)) ez = ez0;
+        Ex[id] = ex;
+        Ey[id] = ey;
+        Ez[id] = ez;
+        if (in_d) {   // snapshot ring for the blocked running DFT
+            T* __restrict__ snap = p.snap + (long long)(n % p.K) * 3 * p.nd + dv;
+            snap[0] = ex;
+            snap[p.nd] = ey;
+            snap[2 * p.nd] = ez;
+        }
+        const T mag = fabs(ex) + fabs(ey) + fabs(ez);
+        if (!(mag < p.blowup)) atomicOr(p.ctl + 2, 1);
+    }
+    // the last block to finish advances the device step counter
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd((unsigned*)(p.ctl + 1), 1u);
+        if (prev == p.nblocks_e - 1) {
+            p.ctl[1] = 0;
+            atomicExch(p.ctl, n + 1);
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Blocked running DFT over the design box.  After cnt steps n0..n0+cnt-1 (n0 = ctl[0] - cnt), each
+// thread owns one design voxel: it reads the cnt snapshots E^{n+1} of its three samples, forms the
+// block sums sum_s E^{n0+s+1} (cos, -sin)(w_f (n0+s+1) dt) in the accumulation type A, and adds
+// them to the FP64 accumulators, which are read and written once per block instead of every step.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct vec2_of;
+template <>
+struct vec2_of<float> {
+    using type = float2;
+};
+template <>
+struct vec2_of<double> {
+    using type = double2;
+};
+
+template <typename T>
+struct DParams {
+    long long nd;
+    int nf, K;
+    const T* snap;                          // [K][3][nd]
+    double2* dft;                           // [nf][3][nd]
+    const typename vec2_of<T>::type* ph;    // (cos, sin)(w_f n dt) in T, [(M+1)][nf]
+    const int* ctl;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) dft_kernel(const DParams<T> d, int cnt)
+{
+    const long long v = (long long)blockIdx.x * kReduceThreads + threadIdx.x;
+    if (v >= d.nd) return;
+    const int n0 = __ldcg(d.ctl) - cnt;
+    T e[kMaxSnap][3];
+#pragma unroll
+    for (int s = 0; s < kMaxSnap; ++s) {
+        if (s < cnt) {
+            const T* sp = d.snap + (long long)((n0 + s) % d.K) * 3 * d.nd + v;
+            e[s][0] = sp[0];
+            e[s][1] = sp[d.nd];
+            e[s][2] = sp[2 * d.nd];
+        }
+    }
+    for (int f = 0; f < d.nf; ++f) {
+        T re[3] = {T(0), T(0), T(0)}, im[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int s = 0; s < kMaxSnap; ++s) {
+            if (s < cnt) {
+                const auto ph = __ldg(d.ph + (long long)(n0 + s + 1) * d.nf + f);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    re[c] = fma(e[s][c], ph.x, re[c]);
+                    im[c] = fma(-e[s][c], ph.y, im[c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2* acc = d.dft + (long long)(f * 3 + c) * d.nd + v;
+            double2 a = *acc;
+            a.x += (double)re[c];
+            a.y += (double)im[c];
+            *acc = a;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gradient: per design voxel v (not gap),
+//   G_v = -sum_c sum_f 2 Re{ (A_cf + (1 - 2 rho_v) B_cf) Ehat_cf,v Lambda_cf,v },
+// A_cf = dY/drho without the gamma term, B_cf = gamma (z+1)/2 (host-precomputed, FP64).
+// The squared norm is reduced per block with warp shuffles into partial[blockIdx.x]; the last
+// block adds the partials in block order (deterministic) into partial[gridDim.x].
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct GParams {
+    int db[6], gb[6];
+    int dnx, dny;
+    long long nd;
+    int nf;
+    const double2* dft_f;
+    const double2* dft_a;
+    const double2* AB;           // [c][f][2]: A, B
+    const T* rho;
+    double* grad64;              // one of grad64 / grad32 is non-null
+    float* grad32;
+    double* partial;             // [gridDim.x + 1]
+    unsigned* counter;
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) grad_kernel(const GParams<T> g)
+{
+    __shared__ double warp_part[kReduceThreads / 32];
+    __shared__ bool last;
+    const long long v = (long long)blockIdx.x * kReduceThreads + threadIdx.x;
+    double G = 0.0;
+    if (v < g.nd) {
+        const int i = g.db[0] + (int)(v % g.dnx);
+        const int j = g.db[2] + (int)((v / g.dnx) % g.dny);
+        const int k = g.db[4] + (int)(v / ((long long)g.dnx * g.dny));
+        if (!in_box(g.gb, i, j, k)) {
+            const double s = 1.0 - 2.0 * (double)g.rho[v];
+            for (int c = 0; c < 3; ++c)
+                for (int f = 0; f < g.nf; ++f) {
+                    const double2 A = __ldg(g.AB + (c * g.nf + f) * 2);
+                    const double2 B = __ldg(g.AB + (c * g.nf + f) * 2 + 1);
+                    const double dyr = A.x + s * B.x, dyi = A.y + s * B.y;
+                    const long long o = (long long)(f * 3 + c) * g.nd + v;
+                    const double2 e = g.dft_f[o], l = g.dft_a[o];
+                    const double eli_r = e.x * l.x - e.y * l.y, eli_i = e.x * l.y + e.y * l.x;
+                    G -= 2.0 * (dyr * eli_r - dyi * eli_i);
+                }
+        }
+        if (g.grad64) g.grad64[v] = G;
+        if (g.grad32) g.grad32[v] = (float)G;
+    }
+    double s2 = warp_sum(G * G);
+    if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) b += warp_part[w];
+        g.partial[blockIdx.x] = b;
+        __threadfence();
+        last = (atomicAdd(g.counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)g.partial)[b];
+        g.partial[gridDim.x] = t;
+        *g.counter = 0;
+    }
+}
+
+}  // namespace fdtd

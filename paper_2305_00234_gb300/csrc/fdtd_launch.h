@@ -1,0 +1,29 @@
+// Host-side declarations of the kernel launch wrappers (defined in fdtd_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdtd_kernels.cuh"
+
+namespace fdtd {
+
+template <typename T>
+cudaError_t launch_h(const KParams<T>& p, cudaStream_t s);
+int pole_bucket(int max_poles);
+template <typename T>
+cudaError_t launch_e(const KParams<T>& p, int bucket, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s);
+unsigned e_blocks(int nx, int ny, int nz);
+template <typename T>
+cudaError_t launch_grad(const GParams<T>& g, unsigned nblocks, cudaStream_t s);
+cudaError_t launch_gap_gather(const double2* dft, long long nd, int nf, const int* db, int dnx, int dny, const int* gb,
+                              double2* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rho_import(const void* src, int dtype, long long n, T* dst, int* flag, cudaStream_t s);
+template <typename T>
+cudaError_t launch_to_double(const T* src, long long n, double* dst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaStream_t s);
+
+}  // namespace fdtd

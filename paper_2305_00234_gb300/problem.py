@@ -1,0 +1,105 @@
+"""Handle-owning wrapper over the C-ABI calls (shapes and dtypes only; no arithmetic)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native as N
+
+
+def box_shape(box):
+    """(dnz, dny, dnx) of a half-open {i0,i1,j0,j1,k0,k1} box (zeros if empty)."""
+    if box[1] <= box[0] or box[3] <= box[2] or box[5] <= box[4]:
+        return (0, 0, 0)
+    return (box[5] - box[4], box[3] - box[2], box[1] - box[0])
+
+
+class Problem:
+    """One gradient problem on the current CUDA device.
+
+    desc: grid description dict (keys of ``fdtd_grid_desc``); bg/m1/m2: material dicts
+    ``{"eps_inf": [3], "sigma": [3], "poles": [[(a, c), ...] x 3]}``; stream: a cudaStream_t
+    handle as int (e.g. ``torch.cuda.current_stream().cuda_stream``) or None.
+    """
+
+    def __init__(self, desc, bg, m1, m2, gamma=0.0, stream=None):
+        self.desc = dict(desc)
+        self.h = N.fdtd_create_grid(desc, stream)
+        try:
+            N.fdtd_set_materials(self.h, bg, m1, m2, gamma)
+        except Exception:
+            self.close()
+            raise
+        self.n = (int(desc["nz"]), int(desc["ny"]), int(desc["nx"]))
+        self.dshape = box_shape(desc["design_box"])
+        self.gshape = box_shape(desc["gap_box"])
+        self.nf = len(desc["freqs_hz"])
+        self.nd = int(np.prod(self.dshape))
+        self.ngap = int(np.prod(self.gshape))
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.fdtd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_density(self, rho):
+        N.fdtd_set_density(self.h, rho)
+
+    def forward(self):
+        ng = 2 * self.nf * 3 * self.ngap
+        F, g = N.fdtd_forward(self.h, ng)
+        return F, (g[0::2] + 1j * g[1::2]).reshape((self.nf, 3) + self.gshape)
+
+    def adjoint(self):
+        N.fdtd_adjoint(self.h)
+
+    def gradient(self, out=None):
+        if out is None:
+            out = np.zeros(self.dshape, dtype=np.float64)
+        N.fdtd_gradient(self.h, out)
+        return out
+
+    def gradient_norm2(self):
+        return N.fdtd_gradient_norm(self.h)
+
+    def field(self, which):
+        return N.fdtd_get_field(self.h, which, int(np.prod(self.n))).reshape(self.n)
+
+    def dft(self, adjoint=False):
+        a = N.fdtd_get_dft(self.h, adjoint, 2 * self.nf * 3 * self.nd)
+        return (a[0::2] + 1j * a[1::2]).reshape((self.nf, 3) + self.dshape)
+
+    def index_map(self, which):
+        shape = ((3,) + self.n) if which <= 1 else self.n
+        return N.fdtd_get_index_map(self.h, which, int(np.prod(shape))).reshape(shape)
+
+    def set_profiling(self, on=True):
+        N.fdtd_set_profiling(self.h, on)
+
+    def timings(self):
+        return N.fdtd_get_timings(self.h)
+
+    def reset_timings(self):
+        N.fdtd_reset_timings(self.h)
+
+    def info(self):
+        return N.fdtd_get_info(self.h)
+
+
+def problem(w, stream=None):
+    """Problem for a workload dict (desc, bg, m1, m2, gamma, rho) with the density set."""
+    p = Problem(w["desc"], w["bg"], w["m1"], w["m2"], w.get("gamma", 0.0), stream)
+    if w.get("rho") is not None:
+        p.set_density(w["rho"])
+    return p
