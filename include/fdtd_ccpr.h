@@ -102,11 +102,14 @@ typedef struct {
 /* Per-kernel device time, measured with CUDA events on the handle's stream while profiling is
  * on (fdtd_set_profiling); launches = kernels this library launched since the last reset. */
 typedef struct {
-    double h_ms, e_ms, dft_ms, grad_ms;      /* summed device time per kernel kind */
-    long long h_launches, e_launches, dft_launches, grad_launches;
+    /* summed device time per kernel kind: H update, E update outside / inside the design box,
+     * blocked DFT, gradient */
+    double h_ms, ebg_ms, ed_ms, dft_ms, grad_ms;
+    long long h_launches, ebg_launches, ed_launches, dft_launches, grad_launches;
     long long launches;                      /* every kernel launch of this library */
     /* algorithmic bytes per launch: each state word read once and written once */
-    double bytes_h_per_launch, bytes_e_per_launch, bytes_dft_per_launch, bytes_grad_per_launch;
+    double bytes_h_per_launch, bytes_ebg_per_launch, bytes_ed_per_launch, bytes_dft_per_launch,
+        bytes_grad_per_launch;
     double dft_steps_per_launch;             /* time steps folded into one DFT launch */
 } fdtd_timings;
 

@@ -10,3 +10,11 @@ from ._native import (FdtdError, fdtd_adjoint, fdtd_cancel, fdtd_create_grid, fd
                       fdtd_gradient_norm, fdtd_last_error, fdtd_reset_timings, fdtd_set_density,
                       fdtd_set_materials, fdtd_set_profiling, load_library)
 from .problem import Problem, box_shape, problem  # noqa: F401
+
+
+def __getattr__(name):
+    # torch is only needed for the autograd wrapper; import it on first use
+    if name in ("FdtdGrad", "objective", "checkpoint_bytes"):
+        from . import grad
+        return getattr(grad, name)
+    raise AttributeError(name)

@@ -45,14 +45,12 @@ class Material(C.Structure):
 
 
 class Timings(C.Structure):
-    _fields_ = [("h_ms", C.c_double), ("e_ms", C.c_double), ("dft_ms", C.c_double),
-                ("grad_ms", C.c_double),
-                ("h_launches", C.c_longlong), ("e_launches", C.c_longlong),
-                ("dft_launches", C.c_longlong), ("grad_launches", C.c_longlong),
-                ("launches", C.c_longlong),
-                ("bytes_h_per_launch", C.c_double), ("bytes_e_per_launch", C.c_double),
-                ("bytes_dft_per_launch", C.c_double), ("bytes_grad_per_launch", C.c_double),
-                ("dft_steps_per_launch", C.c_double)]
+    _fields_ = [(k, C.c_double) for k in ("h_ms", "ebg_ms", "ed_ms", "dft_ms", "grad_ms")] + \
+               [(k, C.c_longlong) for k in ("h_launches", "ebg_launches", "ed_launches", "dft_launches",
+                                            "grad_launches", "launches")] + \
+               [(k, C.c_double) for k in ("bytes_h_per_launch", "bytes_ebg_per_launch", "bytes_ed_per_launch",
+                                          "bytes_dft_per_launch", "bytes_grad_per_launch",
+                                          "dft_steps_per_launch")]
 
 
 class FdtdError(RuntimeError):

@@ -389,6 +389,7 @@ struct Solver : SolverBase {
         p.ctl = ctl;
         for (int m = 0; m < 2; ++m) dp[m].ctl = ctl;
         p.nblocks_e = fdtd::e_blocks(d.nx, d.ny, d.nz);
+        p.nblocks_d = c->nd ? fdtd::design_blocks(c->dn[0], c->dn[1], c->dn[2]) : 0;
         p.blowup = (T)1e30;
         p.tfsf_i0 = -1;
         p.nb = 0;
@@ -614,7 +615,8 @@ struct Solver : SolverBase {
         cudaError_t err = cudaSuccess;
         for (int s = 0; s < steps && err == cudaSuccess; ++s) {
             err = fdtd::launch_h<T>(p, c->work);
-            if (err == cudaSuccess) err = fdtd::launch_e<T>(p, bucket, c->work);
+            if (err == cudaSuccess) err = fdtd::launch_e_bg<T>(p, c->work);
+            if (err == cudaSuccess) err = fdtd::launch_e_design<T>(p, bucket, c->work);
         }
         if (err == cudaSuccess) err = fdtd::launch_dft<T>(dp[mode], steps, c->work);
         cudaError_t e2 = cudaStreamEndCapture(c->work, &g);
@@ -637,8 +639,8 @@ struct Solver : SolverBase {
         const int K = std::min(M, kGraphSteps);
         const int nblk = (M + K - 1) / K;
         if (c->prof) {
-            // events: per step (before H, between H and E, after E), per block one after the DFT
-            const size_t need = 3 * (size_t)M + nblk;
+            // events: per step (before H, after H, after E_bg, after E_design), per block one after the DFT
+            const size_t need = 4 * (size_t)M + nblk;
             while (c->ev.size() < need) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
@@ -648,28 +650,32 @@ struct Solver : SolverBase {
             for (int b = 0; b < nblk; ++b) {
                 const int cnt = std::min(K, M - b * K);
                 for (int q = 0; q < cnt; ++q, ++s) {
-                    CK(cudaEventRecord(c->ev[3 * s], c->work));
+                    CK(cudaEventRecord(c->ev[4 * s], c->work));
                     CK(fdtd::launch_h<T>(p, c->work));
-                    CK(cudaEventRecord(c->ev[3 * s + 1], c->work));
-                    CK(fdtd::launch_e<T>(p, bucket, c->work));
-                    CK(cudaEventRecord(c->ev[3 * s + 2], c->work));
+                    CK(cudaEventRecord(c->ev[4 * s + 1], c->work));
+                    CK(fdtd::launch_e_bg<T>(p, c->work));
+                    CK(cudaEventRecord(c->ev[4 * s + 2], c->work));
+                    CK(fdtd::launch_e_design<T>(p, bucket, c->work));
+                    CK(cudaEventRecord(c->ev[4 * s + 3], c->work));
                 }
                 CK(fdtd::launch_dft<T>(dp[mode], cnt, c->work));
-                CK(cudaEventRecord(c->ev[3 * (size_t)M + b], c->work));
+                CK(cudaEventRecord(c->ev[4 * (size_t)M + b], c->work));
                 if ((s % kChunkSteps) < K && c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
             }
             CK(cudaStreamSynchronize(c->work));
             for (int q = 0; q < M; ++q) {
-                float a = 0, b = 0;
-                CK(cudaEventElapsedTime(&a, c->ev[3 * q], c->ev[3 * q + 1]));
-                CK(cudaEventElapsedTime(&b, c->ev[3 * q + 1], c->ev[3 * q + 2]));
+                float a = 0, b = 0, d = 0;
+                CK(cudaEventElapsedTime(&a, c->ev[4 * q], c->ev[4 * q + 1]));
+                CK(cudaEventElapsedTime(&b, c->ev[4 * q + 1], c->ev[4 * q + 2]));
+                CK(cudaEventElapsedTime(&d, c->ev[4 * q + 2], c->ev[4 * q + 3]));
                 c->tim.h_ms += a;
-                c->tim.e_ms += b;
+                c->tim.ebg_ms += b;
+                c->tim.ed_ms += d;
             }
             for (int b = 0; b < nblk; ++b) {
                 const int last = std::min(M, (b + 1) * K) - 1;
                 float a = 0;
-                CK(cudaEventElapsedTime(&a, c->ev[3 * last + 2], c->ev[3 * (size_t)M + b]));
+                CK(cudaEventElapsedTime(&a, c->ev[4 * last + 3], c->ev[4 * (size_t)M + b]));
                 c->tim.dft_ms += a;
             }
         } else {
@@ -683,12 +689,13 @@ struct Solver : SolverBase {
             if (rem) CK(cudaGraphLaunch(graph[mode][1], c->work));
         }
         c->tim.h_launches += M;
-        c->tim.e_launches += M;
+        c->tim.ebg_launches += M;
+        if (c->nd) c->tim.ed_launches += M;
         if (c->nd) {
             c->tim.dft_launches += nblk;
             c->tim.launches += nblk;
         }
-        c->tim.launches += 2LL * M;
+        c->tim.launches += (c->nd ? 3LL : 2LL) * M;
         int hctl[4];
         CK(cudaMemcpyAsync(hctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
@@ -1180,14 +1187,16 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     fdtd_timings t = h->tim;
     const double ts = h->d.precision == 64 ? 8.0 : 4.0;
     // algorithmic bytes per launch: every state word read once and written once
-    double be = 9.0 * ts * (double)h->ncell;            // E r/w, H read
-    double bh = 9.0 * ts * (double)h->ncell;            // H r/w, E read
+    const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);
+    double bh = 9.0 * ts * nc;                          // H r/w, E read
+    double bbg = 9.0 * ts * (nc - nd);                  // E r/w, H read (outside the design box)
+    double bd = 9.0 * ts * nd;                          // the same inside the design box
     const int n[3] = {h->d.nx, h->d.ny, h->d.nz};
     for (int a = 0; a < 3; ++a) {
         const double w = (double)h->d.cpml[2 * a] + h->d.cpml[2 * a + 1];
-        const double slab = (double)(h->ncell / n[a]) * w;
-        be += 2.0 * 2.0 * ts * slab;                       // two psi_E r/w
-        bh += 2.0 * 2.0 * ts * slab;
+        const double slab = nc / n[a] * w;
+        bbg += 2.0 * 2.0 * ts * slab;                   // two psi_E arrays r/w per attenuated axis
+        bh += 2.0 * 2.0 * ts * slab;                    // two psi_H arrays r/w
     }
     if (h->impl) {
         int P = 0;
@@ -1196,16 +1205,16 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
         } else {
             for (int k = 0; k < 3; ++k) P += as<float>(h)->ptot[k];
         }
-        const double nd = (double)h->nd, nod = (double)(h->nd - h->ngap);
-        be += nod * ts + nod * P * 2.0 * 2.0 * ts;          // rho read, Q r/w (design, non-gap)
-        be += nd * 3.0 * ts;                                // E snapshot write (design box)
+        bd += nod * ts + nod * P * 2.0 * 2.0 * ts;      // rho read, Q r/w (design, non-gap)
+        bd += nd * 3.0 * ts;                            // E snapshot write
         const double K = std::min(h->d.n_steps, kGraphSteps);
         t.dft_steps_per_launch = K;
         t.bytes_dft_per_launch = nd * (K * 3.0 * ts + 3.0 * h->d.n_freq * 16.0 * 2.0);  // snapshots + FP64 acc r/w
         t.bytes_grad_per_launch = nd * (2.0 * 3.0 * h->d.n_freq * 16.0 + ts + 8.0);     // both DFTs, rho, grad
     }
-    t.bytes_e_per_launch = be;
     t.bytes_h_per_launch = bh;
+    t.bytes_ebg_per_launch = bbg;
+    t.bytes_ed_per_launch = bd;
     *out = t;
     return FDTD_OK;
 }

@@ -81,11 +81,12 @@ __global__ void index_map_kernel(const KParams<T> p, int which, int32_t* out)
 }
 
 static dim3 grid3(int nx, int ny, int nz) { return dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY, nz); }
+static dim3 grid_pz(int nx, int ny, int nz) { return grid3(nx, ny, (nz + kPZ - 1) / kPZ); }
 
 template <typename T>
 cudaError_t launch_h(const KParams<T>& p, cudaStream_t s)
 {
-    h_kernel<T><<<grid3(p.nx, p.ny, p.nz), dim3(kBX, kBY), 0, s>>>(p);
+    h_kernel<T><<<grid_pz(p.nx, p.ny, p.nz), dim3(kBX, kBY), 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -95,14 +96,23 @@ int pole_bucket(int max_poles)
 }
 
 template <typename T>
-cudaError_t launch_e(const KParams<T>& p, int bucket, cudaStream_t s)
+cudaError_t launch_e_bg(const KParams<T>& p, cudaStream_t s)
 {
-    const dim3 g = grid3(p.nx, p.ny, p.nz), b(kBX, kBY);
+    e_bg_kernel<T><<<grid_pz(p.nx, p.ny, p.nz), dim3(kBX, kBY), 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_e_design(const KParams<T>& p, int bucket, cudaStream_t s)
+{
+    if (p.nd == 0) return cudaSuccess;
+    const dim3 b(kBX, kBY);
+    const dim3 g = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
     switch (bucket) {
-    case 0: e_kernel<T, 0><<<g, b, 0, s>>>(p); break;
-    case 4: e_kernel<T, 4><<<g, b, 0, s>>>(p); break;
-    case 8: e_kernel<T, 8><<<g, b, 0, s>>>(p); break;
-    default: e_kernel<T, 16><<<g, b, 0, s>>>(p); break;
+    case 0: e_design_kernel<T, 0><<<g, b, 0, s>>>(p); break;
+    case 4: e_design_kernel<T, 4><<<g, b, 0, s>>>(p); break;
+    case 8: e_design_kernel<T, 8><<<g, b, 0, s>>>(p); break;
+    default: e_design_kernel<T, 16><<<g, b, 0, s>>>(p); break;
     }
     return cudaGetLastError();
 }
@@ -117,7 +127,13 @@ cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s)
 
 unsigned e_blocks(int nx, int ny, int nz)
 {
-    const dim3 g = grid3(nx, ny, nz);
+    const dim3 g = grid_pz(nx, ny, nz);
+    return g.x * g.y * g.z;
+}
+
+unsigned design_blocks(int dnx, int dny, int dnz)
+{
+    const dim3 g = grid3(dnx, dny, dnz);
     return g.x * g.y * g.z;
 }
 
@@ -168,7 +184,8 @@ cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaS
 
 #define FDTD_INSTANTIATE(T)                                                                              \
     template cudaError_t launch_h<T>(const KParams<T>&, cudaStream_t);                                   \
-    template cudaError_t launch_e<T>(const KParams<T>&, int, cudaStream_t);                              \
+    template cudaError_t launch_e_bg<T>(const KParams<T>&, cudaStream_t);                                \
+    template cudaError_t launch_e_design<T>(const KParams<T>&, int, cudaStream_t);                       \
     template cudaError_t launch_dft<T>(const DParams<T>&, int, cudaStream_t);                            \
     template cudaError_t launch_grad<T>(const GParams<T>&, unsigned, cudaStream_t);                      \
     template cudaError_t launch_rho_import<T>(const void*, int, long long, T*, int*, cudaStream_t);      \

@@ -1,23 +1,26 @@
 // Device kernels of the CCPR time-domain adjoint gradient (arXiv 2305.00234) for sm_103a.
 //
-// The time step is split into the two memory-bound stencil kernels of the Yee scheme:
-//   h_kernel: H^{n+1/2} = H^{n-1/2} - (dt/mu0) curl E^n                      (Eq. (Maxwells)c)
-//             with CFS-CPML psi only for cells inside the edge slabs;
-//   e_kernel: E^{n+1} from curl H^{n+1/2}, the conductivity and the CCPR pole currents of both
-//             materials weighted by 1-rho and rho (Eqs. (Maxwells)a,b, (eps_mixed),
-//             (sigma_mixed), (Poles_mixed)); the pole recursion
-//             Q <- Q + (alpha-1) Q + beta (E^{n+1}+E^n); the point / TF-SF sources; the running
-//             FP64 DFT of E over the design box, fused so E is not read twice.
+// One Yee time step is three memory-bound stencil launches plus, every kMaxSnap steps, a DFT launch:
+//   h_kernel:        H^{n+1/2} = H^{n-1/2} - (dt/mu0) curl E^n                   (Eq. (Maxwells)c)
+//                    with CFS-CPML psi only for cells inside the edge slabs;
+//   e_bg_kernel:     E^{n+1} outside the design box: background material, CPML, sources;
+//   e_design_kernel: E^{n+1} inside the design box: the conductivity and the CCPR pole currents of
+//                    both materials weighted by 1-rho and rho (Eqs. (Maxwells)a,b, (eps_mixed),
+//                    (sigma_mixed), (Poles_mixed)), the pole recursion
+//                    Q <- Q + (alpha-1) Q + beta (E^{n+1}+E^n), and an E snapshot for the DFT;
+//   dft_kernel:      the running FP64 DFT over the design box, kMaxSnap steps per update;
 // and the per-voxel gradient kernel (structure of Eq. (Gradient_analytic)) with a deterministic
 // warp-shuffle reduction of its squared norm.
 //
-// Thread layout: block (32, 8) over (x, y), one z plane per blockIdx.z; x is the fastest array
-// axis, so each warp reads and writes 128 contiguous bytes per field (FP32).  Neighbour reads
-// at -1 (E kernel) / +1 (H kernel) come from L1/L2: the plane k-1 was touched by blocks
-// scheduled just before, so DRAM sees each array about once per kernel.
+// Thread layout: block (32, 8) over (x, y); x is the fastest array axis, so each warp reads and
+// writes 128 contiguous bytes per field (FP32).  The H and background-E kernels give each thread
+// kPZ consecutive z planes and issue every load before any store, which doubles the loads in
+// flight (the kernels are latency-bound otherwise) and reuses the z neighbour from registers.
+// Neighbour reads at -1 (E) / +1 (H) in x and y come from L1/L2.
 //
 // The step index n lives in device memory (ctl[0]) so that a captured CUDA graph of K steps
-// can be replayed: both kernels read it, and the last E block to finish advances it.
+// can be replayed: every kernel reads it, and the last block of e_design_kernel (of e_bg_kernel
+// when there is no design box) advances it.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,6 +34,19 @@ constexpr int kBX = 32;
 constexpr int kBY = 8;
 constexpr int kReduceThreads = 256;
 constexpr int kMaxSnap = 16;      // steps per blocked DFT update (snapshot ring length)
+#ifndef FDTD_PZ
+#define FDTD_PZ 2
+#endif
+#ifndef FDTD_H_MINB
+#define FDTD_H_MINB 6
+#endif
+#ifndef FDTD_EBG_MINB
+#define FDTD_EBG_MINB 4
+#endif
+#ifndef FDTD_ED_MINB
+#define FDTD_ED_MINB 4
+#endif
+constexpr int kPZ = FDTD_PZ;      // z planes per thread in the H and background E kernels
 
 template <typename T>
 struct cpx {
@@ -76,8 +92,9 @@ struct KParams {
     int tfsf_i0;                 // first total-field x index, -1 = no TF/SF
     const T* einc;               // E_inc^n at x = i0 dx
     const T* hinc;               // H_inc^{n+1/2} at x = (i0 - 1/2) dx
-    int* ctl;                    // [0] step n, [1] finished E blocks, [2] flags (bit 0: unstable)
-    unsigned nblocks_e;
+    int* ctl;                    // [0] step n, [1] finished blocks of the advancing launch, [2] flags
+    unsigned nblocks_e;          // blocks of e_bg_kernel
+    unsigned nblocks_d;          // blocks of e_design_kernel
     T blowup;
 };
 
@@ -180,63 +197,194 @@ __device__ __forceinline__ T point_drive(const KParams<T>& p, int i, int j, int 
 template <typename T>
 __device__ __forceinline__ int read_step(const int* ctl) { return __ldcg(ctl); }
 
+// The last block of the launch that owns the step advance moves the device step counter on.
+__device__ __forceinline__ void finish_step(int* ctl, unsigned nblocks, int n)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd((unsigned*)(ctl + 1), 1u);
+        if (prev == nblocks - 1) {
+            ctl[1] = 0;
+            atomicExch(ctl, n + 1);
+            __threadfence();
+        }
+    }
+}
+
+// H update, kPZ consecutive z planes per thread: all loads of both planes are issued before any
+// store, and the z+1 neighbour of plane r is plane r+1's own E value.
 template <typename T>
-__global__ void __launch_bounds__(kBX * kBY) h_kernel(const KParams<T> p)
+__global__ void __launch_bounds__(kBX * kBY, FDTD_H_MINB) h_kernel(const KParams<T> p)
 {
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k0 = blockIdx.z * kPZ;
     if (i >= p.nx || j >= p.ny) return;
-    const long long id = ((long long)k * p.ny + j) * p.nx + i;
     const T* __restrict__ Ex = p.E[0];
     const T* __restrict__ Ey = p.E[1];
     const T* __restrict__ Ez = p.E[2];
     T* __restrict__ Hx = p.H[0];
     T* __restrict__ Hy = p.H[1];
     T* __restrict__ Hz = p.H[2];
-    const bool ip = i + 1 < p.nx, jp = j + 1 < p.ny, kp = k + 1 < p.nz;
-    // every load first
-    const T ex = Ex[id], ey = Ey[id], ez = Ez[id];
-    const T ex_j = jp ? Ex[id + p.nx] : T(0), ex_k = kp ? Ex[id + p.plane] : T(0);
-    const T ey_i = ip ? Ey[id + 1] : T(0), ey_k = kp ? Ey[id + p.plane] : T(0);
-    const T ez_i = ip ? Ez[id + 1] : T(0), ez_j = jp ? Ez[id + p.nx] : T(0);
-    const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
+    const bool ip = i + 1 < p.nx, jp = j + 1 < p.ny;
+    T ex[kPZ + 1], ey[kPZ + 1];
+    T ez[kPZ], ex_j[kPZ], ez_j[kPZ], ey_i[kPZ], ez_i[kPZ], hx[kPZ], hy[kPZ], hz[kPZ];
+#pragma unroll
+    for (int r = 0; r <= kPZ; ++r) {
+        const int k = k0 + r;
+        const bool ok = k < p.nz;
+        const long long id = ((long long)k * p.ny + j) * p.nx + i;
+        ex[r] = ok ? Ex[id] : T(0);     // beyond the last plane: PEC wall
+        ey[r] = ok ? Ey[id] : T(0);
+        if (r < kPZ) {
+            ez[r] = ok ? Ez[id] : T(0);
+            ex_j[r] = ok && jp ? Ex[id + p.nx] : T(0);
+            ez_j[r] = ok && jp ? Ez[id + p.nx] : T(0);
+            ey_i[r] = ok && ip ? Ey[id + 1] : T(0);
+            ez_i[r] = ok && ip ? Ez[id + 1] : T(0);
+            hx[r] = ok ? Hx[id] : T(0);
+            hy[r] = ok ? Hy[id] : T(0);
+            hz[r] = ok ? Hz[id] : T(0);
+        }
+    }
     const int sx = slab_index(i, p.cpl[0], p.cph[0], p.nx);
     const int sy = slab_index(j, p.cpl[1], p.cph[1], p.ny);
-    const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
     const T idx = p.inv_dx, ch = p.ch;
-    // H_x at (i, j+1/2, k+1/2): (curl E)_x = dEz/dy - dEy/dz
-    T xa = (ez_j - ez) * idx, xb = (ey_k - ey) * idx;
-    // H_y at (i+1/2, j, k+1/2): (curl E)_y = dEx/dz - dEz/dx
-    T ya = (ex_k - ex) * idx, yb = (ez_i - ez) * idx;
-    // H_z at (i+1/2, j+1/2, k): (curl E)_z = dEy/dx - dEx/dy
-    T za = (ey_i - ey) * idx, zb = (ex_j - ex) * idx;
-    if (i == p.tfsf_i0 - 1) yb -= __ldg(p.einc + read_step<T>(p.ctl)) * idx;   // H_y here is scattered field
-    if (sy >= 0) {
-        xa = stretch(xa, p.pmlH[1], sy, p.psiH[0][0] + psi_index(p, i, j, k, 1, sy));
-        zb = stretch(zb, p.pmlH[1], sy, p.psiH[2][1] + psi_index(p, i, j, k, 1, sy));
+#pragma unroll
+    for (int r = 0; r < kPZ; ++r) {
+        const int k = k0 + r;
+        if (k >= p.nz) break;
+        const long long id = ((long long)k * p.ny + j) * p.nx + i;
+        const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
+        // H_x at (i, j+1/2, k+1/2): (curl E)_x = dEz/dy - dEy/dz
+        T xa = (ez_j[r] - ez[r]) * idx, xb = (ey[r + 1] - ey[r]) * idx;
+        // H_y at (i+1/2, j, k+1/2): (curl E)_y = dEx/dz - dEz/dx
+        T ya = (ex[r + 1] - ex[r]) * idx, yb = (ez_i[r] - ez[r]) * idx;
+        // H_z at (i+1/2, j+1/2, k): (curl E)_z = dEy/dx - dEx/dy
+        T za = (ey_i[r] - ey[r]) * idx, zb = (ex_j[r] - ex[r]) * idx;
+        if (i == p.tfsf_i0 - 1) yb -= __ldg(p.einc + read_step<T>(p.ctl)) * idx;   // H_y here is scattered field
+        if (sy >= 0) {
+            xa = stretch(xa, p.pmlH[1], sy, p.psiH[0][0] + psi_index(p, i, j, k, 1, sy));
+            zb = stretch(zb, p.pmlH[1], sy, p.psiH[2][1] + psi_index(p, i, j, k, 1, sy));
+        }
+        if (sz >= 0) {
+            xb = stretch(xb, p.pmlH[2], sz, p.psiH[0][1] + psi_index(p, i, j, k, 2, sz));
+            ya = stretch(ya, p.pmlH[2], sz, p.psiH[1][0] + psi_index(p, i, j, k, 2, sz));
+        }
+        if (sx >= 0) {
+            yb = stretch(yb, p.pmlH[0], sx, p.psiH[1][1] + psi_index(p, i, j, k, 0, sx));
+            za = stretch(za, p.pmlH[0], sx, p.psiH[2][0] + psi_index(p, i, j, k, 0, sx));
+        }
+        Hx[id] = hx[r] - ch * (xa - xb);
+        Hy[id] = hy[r] - ch * (ya - yb);
+        Hz[id] = hz[r] - ch * (za - zb);
     }
-    if (sz >= 0) {
-        xb = stretch(xb, p.pmlH[2], sz, p.psiH[0][1] + psi_index(p, i, j, k, 2, sz));
-        ya = stretch(ya, p.pmlH[2], sz, p.psiH[1][0] + psi_index(p, i, j, k, 2, sz));
-    }
-    if (sx >= 0) {
-        yb = stretch(yb, p.pmlH[0], sx, p.psiH[1][1] + psi_index(p, i, j, k, 0, sx));
-        za = stretch(za, p.pmlH[0], sx, p.psiH[2][0] + psi_index(p, i, j, k, 0, sx));
-    }
-    Hx[id] = hx - ch * (xa - xb);
-    Hy[id] = hy - ch * (ya - yb);
-    Hz[id] = hz - ch * (za - zb);
 }
 
-template <typename T, int MP>
-__global__ void __launch_bounds__(kBX * kBY) e_kernel(const KParams<T> p)
+// E update outside the design box (background material, CPML slabs, sources), kPZ planes per
+// thread.  Cells inside the design box are left to e_design_kernel; blocks wholly inside it exit.
+template <typename T>
+__global__ void __launch_bounds__(kBX * kBY, FDTD_EBG_MINB) e_bg_kernel(const KParams<T> p)
 {
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k0 = blockIdx.z * kPZ;
     const int n = read_step<T>(p.ctl);
-    if (i < p.nx && j < p.ny) {
+    const int bi0 = blockIdx.x * kBX, bj0 = blockIdx.y * kBY;
+    const bool block_in_design = bi0 >= p.db[0] && bi0 + kBX <= p.db[1] && bj0 >= p.db[2] && bj0 + kBY <= p.db[3] &&
+                                 k0 >= p.db[4] && k0 + kPZ <= p.db[5];
+    if (!block_in_design && i < p.nx && j < p.ny) {
+        const T* __restrict__ Hx = p.H[0];
+        const T* __restrict__ Hy = p.H[1];
+        const T* __restrict__ Hz = p.H[2];
+        T* __restrict__ Ex = p.E[0];
+        T* __restrict__ Ey = p.E[1];
+        T* __restrict__ Ez = p.E[2];
+        const bool im = i > 0, jm = j > 0;
+        T hx[kPZ + 1], hy[kPZ + 1];     // index 0 = plane k0-1 (the z-1 neighbour of the first plane)
+        T hz[kPZ], hz_j[kPZ], hz_i[kPZ], hy_i[kPZ], hx_j[kPZ], e0[kPZ][3];
+#pragma unroll
+        for (int r = 0; r <= kPZ; ++r) {
+            const int k = k0 + r - 1;
+            const bool ok = k >= 0 && k < p.nz;
+            const long long id = ((long long)k * p.ny + j) * p.nx + i;
+            hx[r] = ok ? Hx[id] : T(0);
+            hy[r] = ok ? Hy[id] : T(0);
+            if (r > 0) {
+                const int q = r - 1;
+                hz[q] = ok ? Hz[id] : T(0);
+                hz_j[q] = ok && jm ? Hz[id - p.nx] : T(0);
+                hx_j[q] = ok && jm ? Hx[id - p.nx] : T(0);
+                hz_i[q] = ok && im ? Hz[id - 1] : T(0);
+                hy_i[q] = ok && im ? Hy[id - 1] : T(0);
+                e0[q][0] = ok ? Ex[id] : T(0);
+                e0[q][1] = ok ? Ey[id] : T(0);
+                e0[q][2] = ok ? Ez[id] : T(0);
+            }
+        }
+        const int sx = slab_index(i, p.cpl[0], p.cph[0], p.nx);
+        const int sy = slab_index(j, p.cpl[1], p.cph[1], p.ny);
+        const T idx = p.inv_dx;
+        T emax = T(0);
+#pragma unroll
+        for (int r = 0; r < kPZ; ++r) {
+            const int k = k0 + r;
+            if (k >= p.nz || in_box(p.db, i, j, k)) continue;
+            const long long id = ((long long)k * p.ny + j) * p.nx + i;
+            const bool km = k > 0;
+            const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
+            // E_x: dHz/dy - dHy/dz ; E_y: dHx/dz - dHz/dx ; E_z: dHy/dx - dHx/dy
+            T xa = (hz[r] - hz_j[r]) * idx, xb = (hy[r + 1] - hy[r]) * idx;
+            T ya = (hx[r + 1] - hx[r]) * idx, yb = (hz[r] - hz_i[r]) * idx;
+            T za = (hy[r + 1] - hy_i[r]) * idx, zb = (hx[r + 1] - hx_j[r]) * idx;
+            if (i == p.tfsf_i0) za -= __ldg(p.hinc + n) * idx;    // H_y(i0-1/2) is scattered field
+            if (sy >= 0) {
+                xa = stretch(xa, p.pmlE[1], sy, p.psiE[0][0] + psi_index(p, i, j, k, 1, sy));
+                zb = stretch(zb, p.pmlE[1], sy, p.psiE[2][1] + psi_index(p, i, j, k, 1, sy));
+            }
+            if (sz >= 0) {
+                xb = stretch(xb, p.pmlE[2], sz, p.psiE[0][1] + psi_index(p, i, j, k, 2, sz));
+                ya = stretch(ya, p.pmlE[2], sz, p.psiE[1][0] + psi_index(p, i, j, k, 2, sz));
+            }
+            if (sx >= 0) {
+                yb = stretch(yb, p.pmlE[0], sx, p.psiE[1][1] + psi_index(p, i, j, k, 0, sx));
+                za = stretch(za, p.pmlE[0], sx, p.psiE[2][0] + psi_index(p, i, j, k, 0, sx));
+            }
+            T dxv = xa - xb, dyv = ya - yb, dzv = za - zb;
+            if (p.nb > 0 && in_box(p.sb, i, j, k)) {
+                dxv += point_drive(p, i, j, k, 0, n);
+                dyv += point_drive(p, i, j, k, 1, n);
+                dzv += point_drive(p, i, j, k, 2, n);
+            }
+            T ex = p.bg_ca[0] * e0[r][0] + p.bg_cb[0] * dxv;
+            T ey = p.bg_ca[1] * e0[r][1] + p.bg_cb[1] * dyv;
+            T ez = p.bg_ca[2] * e0[r][2] + p.bg_cb[2] * dzv;
+            // PEC walls: components tangential to a wall at index 0 stay zero
+            if (!(jm && km)) ex = e0[r][0];
+            if (!(km && im)) ey = e0[r][1];
+            if (!(im && jm)) ez = e0[r][2];
+            Ex[id] = ex;
+            Ey[id] = ey;
+            Ez[id] = ez;
+            emax = fmax(emax, fabs(ex) + fabs(ey) + fabs(ez));
+        }
+        if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
+    }
+    if (p.nd == 0) finish_step(p.ctl, p.nblocks_e, n);
+}
+
+// E update inside the design box: blended CCPR update of the design voxels, background update of
+// the gap voxels, point sources, and the E snapshot for the blocked DFT.  The design box lies
+// outside the CPML, so there is no psi here.  One cell per thread; owns the step advance.
+template <typename T, int MP>
+__global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const KParams<T> p)
+{
+    const int i = p.db[0] + blockIdx.x * kBX + threadIdx.x;
+    const int j = p.db[2] + blockIdx.y * kBY + threadIdx.y;
+    const int k = p.db[4] + blockIdx.z;
+    const int n = read_step<T>(p.ctl);
+    if (i < p.db[1] && j < p.db[3]) {
         const long long id = ((long long)k * p.ny + j) * p.nx + i;
         const T* __restrict__ Hx = p.H[0];
         const T* __restrict__ Hy = p.H[1];
@@ -245,82 +393,48 @@ __global__ void __launch_bounds__(kBX * kBY) e_kernel(const KParams<T> p)
         T* __restrict__ Ey = p.E[1];
         T* __restrict__ Ez = p.E[2];
         const bool im = i > 0, jm = j > 0, km = k > 0;
-        // every field load first
         const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
         const T hz_j = jm ? Hz[id - p.nx] : T(0), hy_k = km ? Hy[id - p.plane] : T(0);
         const T hx_k = km ? Hx[id - p.plane] : T(0), hz_i = im ? Hz[id - 1] : T(0);
         const T hy_i = im ? Hy[id - 1] : T(0), hx_j = jm ? Hx[id - p.nx] : T(0);
         const T ex0 = Ex[id], ey0 = Ey[id], ez0 = Ez[id];
-        const int sx = slab_index(i, p.cpl[0], p.cph[0], p.nx);
-        const int sy = slab_index(j, p.cpl[1], p.cph[1], p.ny);
-        const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
-        const bool in_d = in_box(p.db, i, j, k);
-        const bool design = in_d && !in_box(p.gb, i, j, k);
-        const long long dv = in_d ? ((long long)(k - p.db[4]) * p.dny + (j - p.db[2])) * p.dnx + (i - p.db[0]) : 0;
+        const long long dv = ((long long)(k - p.db[4]) * p.dny + (j - p.db[2])) * p.dnx + (i - p.db[0]);
+        const bool design = !in_box(p.gb, i, j, k);
         const T rho = design ? p.rho[dv] : T(0);
         const T idx = p.inv_dx;
-        // E_x at (i+1/2, j, k): dHz/dy - dHy/dz
-        T xa = (hz - hz_j) * idx, xb = (hy - hy_k) * idx;
-        // E_y at (i, j+1/2, k): dHx/dz - dHz/dx
-        T ya = (hx - hx_k) * idx, yb = (hz - hz_i) * idx;
-        // E_z at (i, j, k+1/2): dHy/dx - dHx/dy
-        T za = (hy - hy_i) * idx, zb = (hx - hx_j) * idx;
-        if (i == p.tfsf_i0) za -= __ldg(p.hinc + n) * idx;    // H_y(i0-1/2) is scattered field
-        if (sy >= 0) {
-            xa = stretch(xa, p.pmlE[1], sy, p.psiE[0][0] + psi_index(p, i, j, k, 1, sy));
-            zb = stretch(zb, p.pmlE[1], sy, p.psiE[2][1] + psi_index(p, i, j, k, 1, sy));
-        }
-        if (sz >= 0) {
-            xb = stretch(xb, p.pmlE[2], sz, p.psiE[0][1] + psi_index(p, i, j, k, 2, sz));
-            ya = stretch(ya, p.pmlE[2], sz, p.psiE[1][0] + psi_index(p, i, j, k, 2, sz));
-        }
-        if (sx >= 0) {
-            yb = stretch(yb, p.pmlE[0], sx, p.psiE[1][1] + psi_index(p, i, j, k, 0, sx));
-            za = stretch(za, p.pmlE[0], sx, p.psiE[2][0] + psi_index(p, i, j, k, 0, sx));
-        }
-        T dx_ = xa - xb, dy_ = ya - yb, dz_ = za - zb;
+        T dxv = ((hz - hz_j) - (hy - hy_k)) * idx;
+        T dyv = ((hx - hx_k) - (hz - hz_i)) * idx;
+        T dzv = ((hy - hy_i) - (hx - hx_j)) * idx;
+        if (i == p.tfsf_i0) dzv -= __ldg(p.hinc + n) * idx;
         if (p.nb > 0 && in_box(p.sb, i, j, k)) {
-            dx_ += point_drive(p, i, j, k, 0, n);
-            dy_ += point_drive(p, i, j, k, 1, n);
-            dz_ += point_drive(p, i, j, k, 2, n);
+            dxv += point_drive(p, i, j, k, 0, n);
+            dyv += point_drive(p, i, j, k, 1, n);
+            dzv += point_drive(p, i, j, k, 2, n);
         }
         T ex, ey, ez;
         if (design) {
-            ex = design_sample<T, MP>(p, 0, rho, dv, ex0, dx_);
-            ey = design_sample<T, MP>(p, 1, rho, dv, ey0, dy_);
-            ez = design_sample<T, MP>(p, 2, rho, dv, ez0, dz_);
+            ex = design_sample<T, MP>(p, 0, rho, dv, ex0, dxv);
+            ey = design_sample<T, MP>(p, 1, rho, dv, ey0, dyv);
+            ez = design_sample<T, MP>(p, 2, rho, dv, ez0, dzv);
         } else {
-            ex = p.bg_ca[0] * ex0 + p.bg_cb[0] * dx_;
-            ey = p.bg_ca[1] * ey0 + p.bg_cb[1] * dy_;
-            ez = p.bg_ca[2] * ez0 + p.bg_cb[2] * dz_;
+            ex = p.bg_ca[0] * ex0 + p.bg_cb[0] * dxv;
+            ey = p.bg_ca[1] * ey0 + p.bg_cb[1] * dyv;
+            ez = p.bg_ca[2] * ez0 + p.bg_cb[2] * dzv;
         }
-        // PEC walls: components tangential to a wall at index 0 stay zero
         if (!(jm && km)) ex = ex0;
         if (!(km && im)) ey = ey0;
         if (!(im && jm)) ez = ez0;
         Ex[id] = ex;
         Ey[id] = ey;
         Ez[id] = ez;
-        if (in_d) {   // snapshot ring for the blocked running DFT
-            T* __restrict__ snap = p.snap + (long long)(n % p.K) * 3 * p.nd + dv;
-            snap[0] = ex;
-            snap[p.nd] = ey;
-            snap[2 * p.nd] = ez;
-        }
+        T* __restrict__ snap = p.snap + (long long)(n % p.K) * 3 * p.nd + dv;
+        snap[0] = ex;
+        snap[p.nd] = ey;
+        snap[2 * p.nd] = ez;
         const T mag = fabs(ex) + fabs(ey) + fabs(ez);
         if (!(mag < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
-    // the last block to finish advances the device step counter
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd((unsigned*)(p.ctl + 1), 1u);
-        if (prev == p.nblocks_e - 1) {
-            p.ctl[1] = 0;
-            atomicExch(p.ctl, n + 1);
-            __threadfence();
-        }
-    }
+    finish_step(p.ctl, p.nblocks_d, n);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -11,10 +11,13 @@ template <typename T>
 cudaError_t launch_h(const KParams<T>& p, cudaStream_t s);
 int pole_bucket(int max_poles);
 template <typename T>
-cudaError_t launch_e(const KParams<T>& p, int bucket, cudaStream_t s);
+cudaError_t launch_e_bg(const KParams<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_e_design(const KParams<T>& p, int bucket, cudaStream_t s);
 template <typename T>
 cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s);
 unsigned e_blocks(int nx, int ny, int nz);
+unsigned design_blocks(int dnx, int dny, int dnz);
 template <typename T>
 cudaError_t launch_grad(const GParams<T>& g, unsigned nblocks, cudaStream_t s);
 cudaError_t launch_gap_gather(const double2* dft, long long nd, int nf, const int* db, int dnx, int dny, const int* gb,

@@ -1,0 +1,59 @@
+"""torch.autograd wrapper: F(rho) with the hand-written adjoint run as its backward.
+
+forward  = fdtd_set_density + fdtd_forward (the library keeps the FP64 forward DFT over the
+           design box as the only checkpoint: design voxels x 3 x F complex values);
+backward = fdtd_adjoint + fdtd_gradient, scaled by the incoming gradient.
+
+No time history is stored (the paper stores E and Q for every step over the design domain,
+Sec. 2); `checkpoint_bytes` reports both sizes.
+"""
+from __future__ import annotations
+
+import torch
+
+from .problem import Problem
+
+
+class FdtdGrad(torch.autograd.Function):
+    """F = FdtdGrad.apply(rho, problem): rho is a (dnz, dny, dnx) float32/float64 CUDA tensor."""
+
+    @staticmethod
+    def forward(ctx, rho, problem):
+        if not isinstance(problem, Problem):
+            raise TypeError("problem must be a paper_2305_00234_gb300.Problem")
+        problem.set_density(rho.detach().contiguous())
+        F, _ = problem.forward()
+        ctx.problem = problem
+        ctx.rho_meta = (rho.shape, rho.dtype, rho.device)
+        return torch.tensor(F, dtype=torch.float64, device=rho.device)
+
+    @staticmethod
+    def backward(ctx, grad_F):
+        p = ctx.problem
+        shape, dtype, device = ctx.rho_meta
+        p.adjoint()
+        g = torch.empty(shape, dtype=dtype if dtype in (torch.float32, torch.float64) else torch.float32,
+                        device=device)
+        if device.type == "cuda":
+            p.gradient(g)
+        else:
+            import numpy as np
+            g = torch.from_numpy(p.gradient(np.zeros(shape, dtype=np.float64))).to(dtype)
+        return g * grad_F.to(g.dtype), None
+
+
+def objective(rho, problem):
+    """Differentiable F(rho)."""
+    return FdtdGrad.apply(rho, problem)
+
+
+def checkpoint_bytes(problem):
+    """(DFT checkpoint bytes kept between forward and backward, bytes a full E + Q time history
+    over the design box would take at the handle's precision)."""
+    d = problem.desc
+    ts = 4 if d["precision"] == 32 else 8
+    nd = problem.nd
+    dft = nd * 3 * problem.nf * 16
+    per_step = sum(1 + 2 * p for p in problem.poles_total) * ts     # E plus complex Q per component
+    history = nd * d["n_steps"] * per_step
+    return dft, history

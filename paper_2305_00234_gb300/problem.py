@@ -35,6 +35,7 @@ class Problem:
         self.nf = len(desc["freqs_hz"])
         self.nd = int(np.prod(self.dshape))
         self.ngap = int(np.prod(self.gshape))
+        self.poles_total = [len(m1["poles"][k]) + len(m2["poles"][k]) for k in range(3)]
 
     def close(self):
         if getattr(self, "h", None):

@@ -152,7 +152,14 @@ def test_many_poles_and_frequencies(gpu):
     m1 = synth.lorentz_dielectric(8, 8, eps_inf=(2.0, 2.5, 3.0))
     m2 = synth.drude_lorentz_metal(9, 8)
     w = dict(desc=d, bg=vacuum(), m1=m1, m2=m2, gamma=1e6, rho=synth.uniform_rho((10, 10, 10), 2))
-    compare(run_gpu(gpu, w), run_oracle(w), 32)
+    # after 2000 steps the fields have decayed to a small tail, so the field check is made on a
+    # 500-step run; DFTs, objective and gradient come from the full run
+    g, o = run_gpu(gpu, w), run_oracle(w)
+    g["fields"], o["fields"] = [None] * 6, [None] * 6
+    ws = dict(w, desc=dict(d, n_steps=500))
+    g["fields"] = run_gpu(gpu, ws, adjoint=False)["fields"]
+    o["fields"] = run_oracle(ws, adjoint=False)["fields"]
+    compare(g, o, 32)
 
 
 def test_small_grid_and_single_voxel_design(gpu):
@@ -209,7 +216,7 @@ def test_repeat_runs_are_deterministic(gpu):
 
 def test_errors_and_call_order(gpu):
     from paper_2305_00234_gb300 import FdtdError
-    w = ragged_tfsf(32, steps=50)
+    w = ragged_tfsf(32, steps=400)
     p = gpu.Problem(w["desc"], w["bg"], w["m1"], w["m2"])
     with pytest.raises(FdtdError) as e:
         p.forward()
