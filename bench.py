@@ -45,6 +45,11 @@ def parse(argv=None):
     ap.add_argument("--cpu-sample-steps", type=int, default=16,
                     help="time steps of the bounded oracle sample (CPU baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests of the seeded serving stream replayed after the throughput run (0: skip)")
+    ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--precision-study", action="store_true",
+                    help="config 3: FP32 fields + FP64 DFT vs all-FP64 build; prints one JSON line")
     return ap.parse_args(argv)
 
 
@@ -247,6 +252,75 @@ def cpu_baseline(args, w_full):
             "seconds": t2 - t1}
 
 
+def serving_run(args, device):
+    """Replay the first N requests of the seeded serving stream (Poisson, mean 20 req/s; cubic grids
+    48..192, 1500-4000 steps, 1-4 pole pairs) through the continuous-batching server and, as the
+    baseline, one after another on the same GPU."""
+    import synth
+    from paper_2305_00234_gb300 import serve
+    items = synth.serving_stream(n_requests=args.serving_requests)
+    cu = sum(2.0 * it["desc"]["nx"] * it["desc"]["ny"] * it["desc"]["nz"] * it["desc"]["n_steps"] for it in items)
+    server = serve.GradientServer(max_slots=args.serving_slots, device=device)
+    res_s, wall_s = serve.replay_stream(serve.from_stream(items), server)
+    server.close()
+    res_q, wall_q = serve.replay_stream(serve.from_stream(items), None)
+    same = all(a.F == b.F for a, b in zip(res_s, res_q))
+    out = {"requests": len(items), "rate_hz": 20.0, "slots": args.serving_slots,
+           "server": {"grad_evals_per_s": len(items) / wall_s, "Gcell_updates_per_s": cu / wall_s / 1e9,
+                      "wall_s": wall_s, "peak_active": server.peak_active, **serve.latency_stats(res_s)},
+           "sequential": {"grad_evals_per_s": len(items) / wall_q, "Gcell_updates_per_s": cu / wall_q / 1e9,
+                          "wall_s": wall_q, **serve.latency_stats(res_q)},
+           "objective_bitwise_equal_alone_vs_mixed": same}
+    out["speedup_grad_evals_per_s"] = out["server"]["grad_evals_per_s"] / out["sequential"]["grad_evals_per_s"]
+    return out
+
+
+def precision_study(args):
+    """Config 3 in the FP32 build (FP64 DFT and gradient accumulators) and the all-FP64 build:
+    relative L2 of the final fields, the DFTs and dF/drho against the FP64 run."""
+    import numpy as np
+    import torch
+
+    import paper_2305_00234_gb300 as lib
+    import synth
+    w = synth.workload("c3")
+    if args.time_steps:
+        w["desc"]["n_steps"] = args.time_steps
+    out = {}
+    res = {}
+    for prec in (64, 32):
+        d = dict(w["desc"], precision=prec)
+        p = lib.Problem(d, w["bg"], w["m1"], w["m2"], w["gamma"], stream=torch.cuda.current_stream().cuda_stream)
+        p.set_density(w["rho"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F, gap = p.forward()
+        fields = [p.field(c) for c in range(3)]
+        dft = p.dft()
+        p.adjoint()
+        g = p.gradient()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        res[prec] = (F, fields, dft, g)
+        ncell = d["nx"] * d["ny"] * d["nz"]
+        out[f"fp{prec}"] = {"seconds_per_gradient_incl_field_readback": t, "F": F,
+                            "Gcell_updates_per_s": 2.0 * ncell * d["n_steps"] / t / 1e9,
+                            "device_bytes": p.info()["device_bytes"]}
+        p.close()
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+    F64, f64, d64, g64 = res[64]
+    F32, f32, d32, g32 = res[32]
+    out["rel_l2_fp32_vs_fp64"] = {"E_final": rel(np.stack(f32), np.stack(f64)), "forward_dft": rel(d32, d64),
+                                  "objective": abs(F32 - F64) / abs(F64), "dF_drho": rel(g32, g64)}
+    line = {"metric": "precision study (config 3)", "config": {"workload": "config 3: 512x512x384 grid, "
+            "16-cell CPML, 256x256x192 design, 2-pair Lorentz dielectric (eps_inf 11.7/11.7/12.1) | 4-pair "
+            "metal", "time_steps": w["desc"]["n_steps"]}, **out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -393,10 +467,13 @@ def run_ours(args):
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * nd, "d2h_bytes_per_step": 4 * nd,
            "note": "per step: float32 density H2D from pinned memory, float32 gradient D2H to pinned "
                    "memory (plus < 2 KB of gap DFT and adjoint coefficients)"}
+    p.close()
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        serving = serving_run(args, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w)
-    p.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
@@ -405,7 +482,8 @@ def run_ours(args):
                 "gpu_launches": launches, "clocks": clocks,
                 "latency_ms": {"p50": statistics.median(per_step),
                                "p99": float(np.percentile(per_step, 99)), "n": len(per_step),
-                               "note": "single-request gradient latency in the timed loop"}}
+                               "note": "single-request gradient latency in the timed loop"},
+                "serving": serving}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -416,6 +494,8 @@ def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_study:
+        return precision_study(args)
     return run_ours(args)
 
 

@@ -183,6 +183,8 @@ fdtd_status fdtd_get_info(fdtd_handle h, double* dt, size_t* n_design, size_t* n
  * (it returns FDTD_ERR_CANCELLED).  The only call that may come from another thread. */
 fdtd_status fdtd_cancel(fdtd_handle h);
 
+/* Message of the handle's last failed call; with h = NULL, of the calling thread's last failed
+ * call (fdtd_create_grid and fdtd_footprint_bytes have no handle to report through). */
 const char* fdtd_last_error(fdtd_handle h);
 fdtd_status fdtd_destroy(fdtd_handle h);
 

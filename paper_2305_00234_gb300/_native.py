@@ -155,7 +155,7 @@ def fdtd_create_grid(desc, stream=None):
     h = C.c_void_p()
     rc = lib.fdtd_create_grid(C.byref(g), C.c_void_p(stream or 0), C.byref(h))
     if rc != FDTD_OK:
-        raise FdtdError(rc, "fdtd_create_grid: invalid description or allocation failure")
+        raise FdtdError(rc, "fdtd_create_grid: " + lib.fdtd_last_error(None).decode())
     return h
 
 
@@ -167,7 +167,7 @@ def fdtd_footprint_bytes(desc, p_total):
     out = C.c_size_t()
     rc = lib.fdtd_footprint_bytes(C.byref(g), pt, C.byref(out))
     if rc != FDTD_OK:
-        raise FdtdError(rc, "fdtd_footprint_bytes")
+        raise FdtdError(rc, "fdtd_footprint_bytes: " + lib.fdtd_last_error(None).decode())
     return out.value
 
 

@@ -937,6 +937,8 @@ struct Solver : SolverBase {
 // ---------------------------------------------------------------------------------------------
 namespace {
 
+thread_local std::string g_last_error;   // errors of calls without a (live) handle
+
 template <typename F>
 fdtd_status guarded(fdtd_ctx* c, F&& fn)
 {
@@ -944,6 +946,7 @@ fdtd_status guarded(fdtd_ctx* c, F&& fn)
         fn();
         return FDTD_OK;
     } catch (const Err& e) {
+        g_last_error = e.msg;
         if (c) {
             c->err = e.msg;
             if (e.code == FDTD_ERR_CUDA) c->dead = true;
@@ -1243,7 +1246,7 @@ fdtd_status fdtd_cancel(fdtd_handle h)
     return FDTD_OK;
 }
 
-const char* fdtd_last_error(fdtd_handle h) { return h ? h->err.c_str() : "null handle"; }
+const char* fdtd_last_error(fdtd_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
 
 fdtd_status fdtd_destroy(fdtd_handle h)
 {

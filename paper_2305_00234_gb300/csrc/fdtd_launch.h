@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "fdtd_kernels.cuh"
+#include "fdtd_params.h"
 
 namespace fdtd {
 
