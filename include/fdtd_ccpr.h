@@ -183,6 +183,31 @@ fdtd_status fdtd_get_info(fdtd_handle h, double* dt, size_t* n_design, size_t* n
  * (it returns FDTD_ERR_CANCELLED).  The only call that may come from another thread. */
 fdtd_status fdtd_cancel(fdtd_handle h);
 
+/* Gradient for callers that cannot allocate device memory.  Some hosts own all device memory
+ * themselves (a framework that has reserved it for its pool allocator, a plug-in host that forbids
+ * its plug-ins to allocate), and some loops cannot afford the device-wide synchronisation that
+ * cudaMalloc/cudaFree imply; such callers keep the forward and adjoint DFTs in their own buffers
+ * and call this instead of fdtd_gradient.  It computes the same per-voxel dF/drho and squared norm
+ * from caller-owned device buffers and allocates nothing: its scratch (per-block partial sums, a
+ * completion counter and the dY/drho constants) is a 1 MiB static array in device memory, which
+ * every GPU that loads this library holds until the process exits.  The paper has no counterpart;
+ * this is a calling convention, not part of the method.
+ *  dft_fwd, dft_adj: device, (n_freq, 3, dnz, dny, dnx) complex as interleaved (re, im) doubles
+ *    (the layout fdtd_get_dft returns); rho: device, design-box densities, rho_dtype 0 float32 /
+ *    1 float64; design_box, gap_box (nullable): host, half-open, gap voxels get 0;
+ *    dy_drho: host, [3][n_freq] x (A.re, A.im, B.re, B.im) with dY/drho = A + (1 - 2 rho) B;
+ *    grad: device, one double per design voxel (output); grad_norm2: host, nullable (output; when
+ *    given, the call waits for the stream); cuda_stream: cudaStream_t or NULL.
+ *  Limits: n_freq <= 8 and at most 33,513,216 design voxels (the partial sums must fit the
+ *    scratch); beyond them FDTD_ERR_ARG with the reason in fdtd_last_error(NULL).
+ *  The first call on each device looks up the scratch array's device address with that device
+ *    current; make that first call before any stream capture.  All calls share the one array and
+ *    it keeps the previous call's contents (each call clears its counter itself): calls that
+ *    overlap on the GPU, from several threads or streams, race and must be serialised. */
+fdtd_status fdtd_gradient_static(const double* dft_fwd, const double* dft_adj, const void* rho, int rho_dtype,
+                                 const int design_box[6], const int gap_box[6], int n_freq,
+                                 const double* dy_drho, double* grad, double* grad_norm2, void* cuda_stream);
+
 /* Message of the handle's last failed call; with h = NULL, of the calling thread's last failed
  * call (fdtd_create_grid and fdtd_footprint_bytes have no handle to report through). */
 const char* fdtd_last_error(fdtd_handle h);

@@ -20,7 +20,8 @@ STATUS = {0: "FDTD_OK", 1: "FDTD_ERR_ARG", 2: "FDTD_ERR_OOM", 3: "FDTD_ERR_CUDA"
 EXPORTS = ("fdtd_create_grid", "fdtd_footprint_bytes", "fdtd_set_materials", "fdtd_set_density",
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gradient_norm", "fdtd_get_field",
            "fdtd_get_dft", "fdtd_get_index_map", "fdtd_set_profiling", "fdtd_get_timings",
-           "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy")
+           "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy",
+           "fdtd_gradient_static")
 
 
 class GridDesc(C.Structure):
@@ -91,6 +92,7 @@ def load_library():
         "fdtd_cancel": [vp],
         "fdtd_last_error": [vp],
         "fdtd_destroy": [vp],
+        "fdtd_gradient_static": [vp, vp, vp, i, P(C.c_int), P(C.c_int), i, P(d), vp, P(d), vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -269,6 +271,29 @@ def fdtd_cancel(h):
 def fdtd_last_error(h):
     m = load_library().fdtd_last_error(h)
     return m.decode() if m else ""
+
+
+def fdtd_gradient_static(dft_fwd, dft_adj, rho, design_box, gap_box, n_freq, dy_drho, grad, stream=None):
+    """No-allocation gradient from caller-owned device buffers (torch CUDA tensors): dft_fwd,
+    dft_adj float64 (interleaved complex), rho float32/float64, grad float64 (written).  dy_drho:
+    host array (3, n_freq, 4).  Returns the squared norm of the gradient."""
+    import torch
+    for t in (dft_fwd, dft_adj, grad):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("dft_fwd, dft_adj and grad must be contiguous float64 CUDA tensors")
+    if not (rho.is_cuda and rho.is_contiguous() and rho.dtype in (torch.float32, torch.float64)):
+        raise TypeError("rho must be a contiguous float32/float64 CUDA tensor")
+    db = (C.c_int * 6)(*[int(x) for x in design_box])
+    gb = (C.c_int * 6)(*[int(x) for x in gap_box]) if gap_box is not None else None
+    cst = np.ascontiguousarray(dy_drho, dtype=np.float64).ravel()
+    norm2 = C.c_double()
+    rc = load_library().fdtd_gradient_static(C.c_void_p(dft_fwd.data_ptr()), C.c_void_p(dft_adj.data_ptr()),
+                                             C.c_void_p(rho.data_ptr()), 0 if rho.dtype == torch.float32 else 1,
+                                             db, gb, int(n_freq), _dptr(cst), C.c_void_p(grad.data_ptr()),
+                                             C.byref(norm2), C.c_void_p(stream or 0))
+    if rc != FDTD_OK:
+        raise FdtdError(rc, load_library().fdtd_last_error(None).decode())
+    return norm2.value
 
 
 def fdtd_destroy(h):

@@ -964,6 +964,15 @@ fdtd_status guarded(fdtd_ctx* c, F&& fn)
 template <typename T>
 Solver<T>* as(fdtd_ctx* c) { return static_cast<Solver<T>*>(c->impl.get()); }
 
+}  // namespace
+
+namespace fdtd {
+// Error text for handle-less calls in other translation units (read by fdtd_last_error(NULL)).
+void set_thread_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace fdtd
+
+namespace {
+
 // Dispatch on the handle's precision.
 template <typename F>
 void dispatch(fdtd_ctx* c, F&& fn)
