@@ -99,8 +99,10 @@ typedef struct {
     const double* c_im[3];
 } fdtd_ccpr_material;
 
-/* Per-kernel device time, measured with CUDA events on the handle's stream while profiling is
- * on (fdtd_set_profiling); launches = kernels this library launched since the last reset. */
+/* Per-kernel device time, measured with CUDA events on the handle's stream while profiling is on
+ * (fdtd_set_profiling): one 16-step block in four is launched kernel by kernel between events,
+ * the others as CUDA graphs.  *_ms sum and *_launches count those timed launches (grad: every
+ * launch); launches counts every kernel this library launched since the last reset. */
 typedef struct {
     /* summed device time per kernel kind: H update, E update outside / inside the design box,
      * blocked DFT, gradient */
@@ -170,8 +172,8 @@ fdtd_status fdtd_get_field(fdtd_handle h, int which, double* dst, size_t n);
 fdtd_status fdtd_get_dft(fdtd_handle h, int adjoint, double* dst, size_t n_doubles);
 fdtd_status fdtd_get_index_map(fdtd_handle h, int which, int32_t* dst, size_t n);
 
-/* Profiling: when on, runs launch kernels one by one (no CUDA graph) with CUDA events around
- * each kernel; fdtd_get_timings returns the sums since fdtd_reset_timings. */
+/* Profiling: when on, runs time a sample of their kernel launches with CUDA events (see
+ * fdtd_timings); fdtd_get_timings returns the sums since fdtd_reset_timings. */
 fdtd_status fdtd_set_profiling(fdtd_handle h, int on);
 fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out);
 fdtd_status fdtd_reset_timings(fdtd_handle h);
@@ -207,6 +209,22 @@ fdtd_status fdtd_cancel(fdtd_handle h);
 fdtd_status fdtd_gradient_static(const double* dft_fwd, const double* dft_adj, const void* rho, int rho_dtype,
                                  const int design_box[6], const int gap_box[6], int n_freq,
                                  const double* dy_drho, double* grad, double* grad_norm2, void* cuda_stream);
+
+/* Density filter and projection on a design-box array (Sec. "Filtering and projection"):
+ *   rho_t = Eq. (FilterFunction): the cone-weighted mean of rho over the sphere |r_m - r_n| < R,
+ *           weight w = R - |r_m - r_n| (distances in voxels), neighbourhoods cut at the box faces;
+ *   rho_b = Eq. (Projection): (tanh(beta eta) + tanh(beta (rho_t - eta))) / (tanh(beta eta) + tanh(beta (1 - eta))).
+ * rho, rho_t, rho_b: device float32 arrays (nz, ny, nx), x fastest; R in (0, 12] voxels, beta > 0,
+ * eta in [0, 1]; work is ordered on cuda_stream (temporary buffers come from the stream-ordered
+ * allocator).  Errors: FDTD_ERR_ARG, text in fdtd_last_error(NULL). */
+fdtd_status fdtd_filter_project(const float* rho, float* rho_t, float* rho_b, int nx, int ny, int nz, double R,
+                                double beta, double eta, void* cuda_stream);
+
+/* Chain rule through filter and projection, Eq. (GradientsFiltered): dF/drho[n] =
+ * sum_m dF/drho_b[m] (d rho_b/d rho_t)[m] w(m,n) / sum_k w(m,k), from rho_t of fdtd_filter_project and
+ * dF/drho_b (e.g. fdtd_gradient's output).  Same layout and limits as fdtd_filter_project. */
+fdtd_status fdtd_filter_project_grad(const float* rho_t, const float* dF_drho_b, float* dF_drho, int nx, int ny,
+                                     int nz, double R, double beta, double eta, void* cuda_stream);
 
 /* Message of the handle's last failed call; with h = NULL, of the calling thread's last failed
  * call (fdtd_create_grid and fdtd_footprint_bytes have no handle to report through). */

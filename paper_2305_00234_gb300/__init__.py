@@ -5,7 +5,8 @@ The compute path is the CUDA library ``libfdtdccpr.so`` (C-ABI: include/fdtd_ccp
 package only marshals arguments to it.  There is no CPU fallback.
 """
 from ._native import (FdtdError, fdtd_adjoint, fdtd_cancel, fdtd_create_grid, fdtd_destroy,  # noqa: F401
-                      fdtd_footprint_bytes, fdtd_forward, fdtd_get_dft, fdtd_get_field,
+                      fdtd_filter_project, fdtd_filter_project_grad, fdtd_footprint_bytes, fdtd_forward,
+                      fdtd_get_dft, fdtd_get_field, fdtd_gradient_static,
                       fdtd_get_index_map, fdtd_get_info, fdtd_get_timings, fdtd_gradient,
                       fdtd_gradient_norm, fdtd_last_error, fdtd_reset_timings, fdtd_set_density,
                       fdtd_set_materials, fdtd_set_profiling, load_library)
@@ -14,7 +15,7 @@ from .problem import Problem, box_shape, problem  # noqa: F401
 
 def __getattr__(name):
     # torch is only needed for the autograd wrapper; import it on first use
-    if name in ("FdtdGrad", "objective", "checkpoint_bytes"):
+    if name in ("FdtdGrad", "FilterProject", "objective", "checkpoint_bytes"):
         from . import grad
         return getattr(grad, name)
     raise AttributeError(name)

@@ -21,7 +21,7 @@ EXPORTS = ("fdtd_create_grid", "fdtd_footprint_bytes", "fdtd_set_materials", "fd
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gradient_norm", "fdtd_get_field",
            "fdtd_get_dft", "fdtd_get_index_map", "fdtd_set_profiling", "fdtd_get_timings",
            "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy",
-           "fdtd_gradient_static")
+           "fdtd_gradient_static", "fdtd_filter_project", "fdtd_filter_project_grad")
 
 
 class GridDesc(C.Structure):
@@ -93,6 +93,8 @@ def load_library():
         "fdtd_last_error": [vp],
         "fdtd_destroy": [vp],
         "fdtd_gradient_static": [vp, vp, vp, i, P(C.c_int), P(C.c_int), i, P(d), vp, P(d), vp],
+        "fdtd_filter_project": [vp, vp, vp, i, i, i, d, d, d, vp],
+        "fdtd_filter_project_grad": [vp, vp, vp, i, i, i, d, d, d, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -294,6 +296,31 @@ def fdtd_gradient_static(dft_fwd, dft_adj, rho, design_box, gap_box, n_freq, dy_
     if rc != FDTD_OK:
         raise FdtdError(rc, load_library().fdtd_last_error(None).decode())
     return norm2.value
+
+
+def _f32_dev(t, name):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def fdtd_filter_project(rho, rho_t, rho_b, R, beta, eta, stream=None):
+    """Filter + projection of a (nz, ny, nx) float32 CUDA tensor into rho_t, rho_b (same shape)."""
+    nz, ny, nx = rho.shape
+    rc = load_library().fdtd_filter_project(_f32_dev(rho, "rho"), _f32_dev(rho_t, "rho_t"), _f32_dev(rho_b, "rho_b"),
+                                            nx, ny, nz, float(R), float(beta), float(eta), C.c_void_p(stream or 0))
+    if rc != FDTD_OK:
+        raise FdtdError(rc, load_library().fdtd_last_error(None).decode())
+
+
+def fdtd_filter_project_grad(rho_t, dF_drho_b, dF_drho, R, beta, eta, stream=None):
+    nz, ny, nx = rho_t.shape
+    rc = load_library().fdtd_filter_project_grad(_f32_dev(rho_t, "rho_t"), _f32_dev(dF_drho_b, "dF_drho_b"),
+                                                 _f32_dev(dF_drho, "dF_drho"), nx, ny, nz, float(R), float(beta),
+                                                 float(eta), C.c_void_p(stream or 0))
+    if rc != FDTD_OK:
+        raise FdtdError(rc, load_library().fdtd_last_error(None).decode())
 
 
 def fdtd_destroy(h):

@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,6 +41,7 @@ const double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
 const double kPi = 3.14159265358979323846;
 constexpr int kGraphSteps = fdtd::kMaxSnap;   // one DFT block per captured graph
 constexpr int kChunkSteps = 512;
+constexpr int kProfEvery = 4;                  // profiling times one DFT block in four
 
 struct Err {
     fdtd_status code;
@@ -196,6 +198,32 @@ size_t footprint(const fdtd_grid_desc& d, const int ptot[3])
     return b;
 }
 
+// Library-private stream-ordered memory pool per device.  Handles allocate and free on their own
+// stream, so creating or destroying one never synchronises the device (cudaFree does), and freed
+// memory stays in the pool for the next handle instead of going back to the driver.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t device_pool(int device)
+{
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (device < 0 || device >= kMaxDevices) throw Err{FDTD_ERR_ARG, "device ordinal above 63"};
+    if (!g_pool[device]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        CK(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~0ull;
+        CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[device] = pool;
+    }
+    return g_pool[device];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -229,9 +257,10 @@ struct fdtd_ctx {
     {
         void* p = nullptr;
         if (n == 0) n = 16;
-        if (cudaMalloc(&p, n) != cudaSuccess) {
+        n = (n + 255) & ~size_t(255);
+        if (cudaMallocFromPoolAsync(&p, n, device_pool(device), work) != cudaSuccess) {
             cudaGetLastError();
-            throw Err{FDTD_ERR_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
+            throw Err{FDTD_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed"};
         }
         allocs.push_back(p);
         bytes += n;
@@ -239,7 +268,7 @@ struct fdtd_ctx {
     }
     void free_all()
     {
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs) cudaFreeAsync(p, work);
         allocs.clear();
     }
 };
@@ -338,8 +367,8 @@ struct Solver : SolverBase {
             }
             T* de = talloc(te.size());
             T* dh = talloc(th.size());
-            CK(cudaMemcpy(de, te.data(), te.size() * sizeof(T), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(dh, th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync(de, te.data(), te.size() * sizeof(T), cudaMemcpyHostToDevice, c->work));
+            CK(cudaMemcpyAsync(dh, th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice, c->work));
             p.pmlE[a] = de;
             p.pmlH[a] = dh;
         }
@@ -348,7 +377,7 @@ struct Solver : SolverBase {
         rho = talloc(c->nd);
         p.rho = rho;
         poles = (PoleTable<T>*)c->alloc(sizeof(PoleTable<T>));
-        CK(cudaMemset(poles, 0, sizeof(PoleTable<T>)));
+        CK(cudaMemsetAsync(poles, 0, sizeof(PoleTable<T>), c->work));
         p.poles = poles;
         int pmax = 0;
         for (int k = 0; k < 3; ++k) {
@@ -370,7 +399,7 @@ struct Solver : SolverBase {
                     ph[(size_t)s * d.n_freq + f] = v;
                 }
             phase = (V2*)c->alloc(ph.size() * sizeof(V2));
-            CK(cudaMemcpy(phase, ph.data(), ph.size() * sizeof(V2), cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync(phase, ph.data(), ph.size() * sizeof(V2), cudaMemcpyHostToDevice, c->work));
         }
         p.K = fdtd::kMaxSnap;
         snap = talloc((size_t)fdtd::kMaxSnap * 3 * c->nd);
@@ -385,7 +414,7 @@ struct Solver : SolverBase {
             dp[m].ph = phase;
         }
         ctl = (int*)c->alloc(4 * sizeof(int));
-        CK(cudaMemset(ctl, 0, 4 * sizeof(int)));
+        CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), c->work));
         p.ctl = ctl;
         for (int m = 0; m < 2; ++m) dp[m].ctl = ctl;
         p.nblocks_e = fdtd::e_blocks(d.nx, d.ny, d.nz);
@@ -396,8 +425,8 @@ struct Solver : SolverBase {
         std::fill(p.sb, p.sb + 6, 0);
         einc = talloc(d.n_steps);
         hinc = talloc(d.n_steps);
-        CK(cudaMemset(einc, 0, d.n_steps * sizeof(T)));
-        CK(cudaMemset(hinc, 0, d.n_steps * sizeof(T)));
+        CK(cudaMemsetAsync(einc, 0, d.n_steps * sizeof(T), c->work));
+        CK(cudaMemsetAsync(hinc, 0, d.n_steps * sizeof(T), c->work));
         p.einc = einc;
         p.hinc = hinc;
         // point-source tables: forward (1 basis, 1 voxel box), adjoint (2F bases, gap box)
@@ -410,7 +439,7 @@ struct Solver : SolverBase {
         const size_t nblk = (c->nd + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads;
         partial = (double*)c->alloc((nblk + 1) * sizeof(double));
         counter = (unsigned*)c->alloc(sizeof(unsigned));
-        CK(cudaMemset(counter, 0, sizeof(unsigned)));
+        CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), c->work));
         AB = (double2*)c->alloc(3 * d.n_freq * 2 * sizeof(double2));
         pf = base;
         pa = base;
@@ -424,8 +453,8 @@ struct Solver : SolverBase {
             std::vector<T> w(d.n_steps), r(3, T(0));
             for (int s = 0; s < d.n_steps; ++s) w[s] = (T)src_pulse(d, (s + 0.5) * c->dt);
             r[d.src_comp] = (T)(d.src_amp * kEps0 / c->dt);
-            CK(cudaMemcpy(src_wave[0], w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(src_r[0], r.data(), 3 * sizeof(T), cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync(src_wave[0], w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, c->work));
+            CK(cudaMemcpyAsync(src_r[0], r.data(), 3 * sizeof(T), cudaMemcpyHostToDevice, c->work));
             pf.nb = 1;
             pf.src_r = src_r[0];
             pf.src_wave = src_wave[0];
@@ -462,8 +491,8 @@ struct Solver : SolverBase {
             for (int m = 1; m < L; ++m) e[m] = (Dm * e[m] + (h[m] - h[m - 1]) / dx) / Dp;
             e[0] = d.src_amp * src_pulse(d, (s + 1) * dt);
         }
-        CK(cudaMemcpy(einc, ei.data(), M * sizeof(T), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(hinc, hi.data(), M * sizeof(T), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(einc, ei.data(), M * sizeof(T), cudaMemcpyHostToDevice, c->work));
+        CK(cudaMemcpyAsync(hinc, hi.data(), M * sizeof(T), cudaMemcpyHostToDevice, c->work));
     }
 
     void set_materials(const Material& bg, const Material& m1, const Material& m2, double gamma)
@@ -533,8 +562,8 @@ struct Solver : SolverBase {
         }
         if (!(gamma >= 0.0)) arg_error("gamma must be >= 0");
         base.hg = (T)(0.5 * gamma);
-        CK(cudaMemcpy(poles, &tab, sizeof tab, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(AB, ab.data(), ab.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(poles, &tab, sizeof tab, cudaMemcpyHostToDevice, c->work));
+        CK(cudaMemcpyAsync(AB, ab.data(), ab.size() * sizeof(double2), cudaMemcpyHostToDevice, c->work));
         build_incident(bg);
         refresh_params();
     }
@@ -638,17 +667,26 @@ struct Solver : SolverBase {
         const KParams<T>& p = mode ? pa : pf;
         const int K = std::min(M, kGraphSteps);
         const int nblk = (M + K - 1) / K;
+        const int full = M / K, rem = M % K;
+        if (!graph[mode][0]) capture(mode, 0, K);
+        if (rem && !graph[mode][1]) capture(mode, 1, rem);
+        // Profiling samples one 16-step block in kProfEvery: its kernels are launched one by one
+        // between CUDA events; every other block is a graph replay, as without profiling.
+        int timed_steps = 0, timed_blocks = 0;
+        std::vector<int> sampled;
         if (c->prof) {
-            // events: per step (before H, after H, after E_bg, after E_design), per block one after the DFT
             const size_t need = 4 * (size_t)M + nblk;
             while (c->ev.size() < need) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
                 c->ev.push_back(e);
             }
-            int s = 0;
-            for (int b = 0; b < nblk; ++b) {
-                const int cnt = std::min(K, M - b * K);
+        }
+        int s = 0;
+        for (int b = 0; b < nblk; ++b) {
+            const int cnt = b < full ? K : rem;
+            if (c->prof && b % kProfEvery == 0) {
+                sampled.push_back(b);
                 for (int q = 0; q < cnt; ++q, ++s) {
                     CK(cudaEventRecord(c->ev[4 * s], c->work));
                     CK(fdtd::launch_h<T>(p, c->work));
@@ -660,42 +698,40 @@ struct Solver : SolverBase {
                 }
                 CK(fdtd::launch_dft<T>(dp[mode], cnt, c->work));
                 CK(cudaEventRecord(c->ev[4 * (size_t)M + b], c->work));
-                if ((s % kChunkSteps) < K && c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
+            } else {
+                CK(cudaGraphLaunch(graph[mode][b < full ? 0 : 1], c->work));
+                s += cnt;
             }
-            CK(cudaStreamSynchronize(c->work));
-            for (int q = 0; q < M; ++q) {
-                float a = 0, b = 0, d = 0;
-                CK(cudaEventElapsedTime(&a, c->ev[4 * q], c->ev[4 * q + 1]));
-                CK(cudaEventElapsedTime(&b, c->ev[4 * q + 1], c->ev[4 * q + 2]));
-                CK(cudaEventElapsedTime(&d, c->ev[4 * q + 2], c->ev[4 * q + 3]));
-                c->tim.h_ms += a;
-                c->tim.ebg_ms += b;
-                c->tim.ed_ms += d;
-            }
-            for (int b = 0; b < nblk; ++b) {
-                const int last = std::min(M, (b + 1) * K) - 1;
-                float a = 0;
-                CK(cudaEventElapsedTime(&a, c->ev[4 * last + 3], c->ev[4 * (size_t)M + b]));
-                c->tim.dft_ms += a;
-            }
-        } else {
-            const int full = M / K, rem = M % K;
-            if (!graph[mode][0]) capture(mode, 0, K);
-            if (rem && !graph[mode][1]) capture(mode, 1, rem);
-            for (int r = 0; r < full; ++r) {
-                CK(cudaGraphLaunch(graph[mode][0], c->work));
-                if (((r + 1) * K) % kChunkSteps < K && c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
-            }
-            if (rem) CK(cudaGraphLaunch(graph[mode][1], c->work));
+            if ((s % kChunkSteps) < K && c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
         }
-        c->tim.h_launches += M;
-        c->tim.ebg_launches += M;
-        if (c->nd) c->tim.ed_launches += M;
+        if (c->prof) {
+            CK(cudaStreamSynchronize(c->work));
+            for (int b : sampled) {
+                const int first = b * K, cnt = std::min(K, M - b * K);
+                for (int q = first; q < first + cnt; ++q) {
+                    float x = 0, y = 0, z = 0;
+                    CK(cudaEventElapsedTime(&x, c->ev[4 * q], c->ev[4 * q + 1]));
+                    CK(cudaEventElapsedTime(&y, c->ev[4 * q + 1], c->ev[4 * q + 2]));
+                    CK(cudaEventElapsedTime(&z, c->ev[4 * q + 2], c->ev[4 * q + 3]));
+                    c->tim.h_ms += x;
+                    c->tim.ebg_ms += y;
+                    c->tim.ed_ms += z;
+                }
+                float w = 0;
+                CK(cudaEventElapsedTime(&w, c->ev[4 * (first + cnt - 1) + 3], c->ev[4 * (size_t)M + b]));
+                c->tim.dft_ms += w;
+                timed_steps += cnt;
+                timed_blocks += 1;
+            }
+        }
+        c->tim.h_launches += timed_steps;          // launches that were timed (profiling samples)
+        c->tim.ebg_launches += timed_steps;
+        if (c->nd) c->tim.ed_launches += timed_steps;
         if (c->nd) {
-            c->tim.dft_launches += nblk;
+            c->tim.dft_launches += timed_blocks;
             c->tim.launches += nblk;
         }
-        c->tim.launches += (c->nd ? 3LL : 2LL) * M;
+        c->tim.launches += (c->nd ? 3LL : 2LL) * M;  // every kernel this run launched
         int hctl[4];
         CK(cudaMemcpyAsync(hctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
@@ -922,11 +958,11 @@ struct Solver : SolverBase {
     void index_map(int which, int32_t* dst, size_t n)
     {
         int32_t* dev = nullptr;
-        CK(cudaMalloc(&dev, n * sizeof(int32_t)));
+        CK(cudaMallocFromPoolAsync((void**)&dev, n * sizeof(int32_t), device_pool(c->device), c->work));
         cudaError_t e = fdtd::launch_index_map<T>(pf, which, dev, c->work);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dst, dev, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->work);
+        cudaFreeAsync(dev, c->work);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
-        cudaFree(dev);
         c->tim.launches++;
         CK(e);
     }
@@ -1077,6 +1113,7 @@ fdtd_status fdtd_set_materials(fdtd_handle h, const fdtd_ccpr_material* bg, cons
             }
         }
         dispatch(h, [&](auto* s) { s->set_materials(B, A1, A2, gamma); });
+        CK(cudaStreamSynchronize(h->work));
         h->has_mat = true;
         h->has_fwd = h->has_adj = h->has_grad = false;
     });
@@ -1263,7 +1300,10 @@ fdtd_status fdtd_destroy(fdtd_handle h)
     cudaSetDevice(h->device);
     if (h->work) cudaStreamSynchronize(h->work);
     h->impl.reset();
-    h->free_all();
+    if (h->work) {
+        h->free_all();
+        cudaStreamSynchronize(h->work);
+    }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->fence) cudaEventDestroy(h->fence);
     if (h->work) cudaStreamDestroy(h->work);

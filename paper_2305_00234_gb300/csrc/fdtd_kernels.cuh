@@ -140,6 +140,30 @@ __device__ __forceinline__ void finish_step(int* ctl, unsigned nblocks, int n)
     }
 }
 
+// A block tile [bi0, bi0+kBX) x [bj0, bj0+kBY) x [k0, k0+kPZ) is interior for the H update when
+// its +1 neighbours exist and no cell lies in a CPML slab or next to the TF/SF plane.
+template <typename T>
+__device__ __forceinline__ bool h_block_interior(const KParams<T>& p, int bi0, int bj0, int k0)
+{
+    return bi0 >= p.cpl[0] && bi0 + kBX < p.nx - p.cph[0] && bj0 >= p.cpl[1] && bj0 + kBY < p.ny - p.cph[1] &&
+           k0 >= p.cpl[2] && k0 + kPZ < p.nz - p.cph[2] && !(p.tfsf_i0 - 1 >= bi0 && p.tfsf_i0 - 1 < bi0 + kBX);
+}
+
+// ... and interior for the background E update when its -1 neighbours exist (no PEC wall), no cell
+// lies in a CPML slab, on the TF/SF plane, in the point-source box or in the design box.
+template <typename T>
+__device__ __forceinline__ bool e_block_interior(const KParams<T>& p, int bi0, int bj0, int k0)
+{
+    const bool slab_free = bi0 >= p.cpl[0] && bi0 >= 1 && bi0 + kBX <= p.nx - p.cph[0] && bj0 >= p.cpl[1] && bj0 >= 1 &&
+                           bj0 + kBY <= p.ny - p.cph[1] && k0 >= p.cpl[2] && k0 >= 1 && k0 + kPZ <= p.nz - p.cph[2];
+    const bool no_plane = !(p.tfsf_i0 >= bi0 && p.tfsf_i0 < bi0 + kBX);
+    const bool no_src = p.nb == 0 || p.sb[1] <= bi0 || p.sb[0] >= bi0 + kBX || p.sb[3] <= bj0 || p.sb[2] >= bj0 + kBY ||
+                        p.sb[5] <= k0 || p.sb[4] >= k0 + kPZ;
+    const bool no_design = p.db[1] <= bi0 || p.db[0] >= bi0 + kBX || p.db[3] <= bj0 || p.db[2] >= bj0 + kBY ||
+                           p.db[5] <= k0 || p.db[4] >= k0 + kPZ;
+    return slab_free && no_plane && no_src && no_design;
+}
+
 // H update, kPZ consecutive z planes per thread: all loads of both planes are issued before any
 // store, and the z+1 neighbour of plane r is plane r+1's own E value.
 template <typename T>
@@ -155,6 +179,37 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_H_MINB) h_kernel(const KParams
     T* __restrict__ Hx = p.H[0];
     T* __restrict__ Hy = p.H[1];
     T* __restrict__ Hz = p.H[2];
+    if (h_block_interior(p, blockIdx.x * kBX, blockIdx.y * kBY, k0)) {
+        // no wall, CPML slab or TF/SF plane anywhere in this block: plain stencil, 32-bit indices
+        const int nx = p.nx, pl = (int)p.plane;
+        const int id0 = (k0 * p.ny + j) * nx + i;
+        T fex[kPZ + 1], fey[kPZ + 1], fez[kPZ], fexj[kPZ], fezj[kPZ], feyi[kPZ], fezi[kPZ], fhx[kPZ], fhy[kPZ], fhz[kPZ];
+#pragma unroll
+        for (int r = 0; r <= kPZ; ++r) {
+            const int id = id0 + r * pl;
+            fex[r] = Ex[id];
+            fey[r] = Ey[id];
+            if (r < kPZ) {
+                fez[r] = Ez[id];
+                fexj[r] = Ex[id + nx];
+                fezj[r] = Ez[id + nx];
+                feyi[r] = Ey[id + 1];
+                fezi[r] = Ez[id + 1];
+                fhx[r] = Hx[id];
+                fhy[r] = Hy[id];
+                fhz[r] = Hz[id];
+            }
+        }
+        const T c = p.ch * p.inv_dx;
+#pragma unroll
+        for (int r = 0; r < kPZ; ++r) {
+            const int id = id0 + r * pl;
+            Hx[id] = fhx[r] - c * ((fezj[r] - fez[r]) - (fey[r + 1] - fey[r]));
+            Hy[id] = fhy[r] - c * ((fex[r + 1] - fex[r]) - (fezi[r] - fez[r]));
+            Hz[id] = fhz[r] - c * ((feyi[r] - fey[r]) - (fexj[r] - fex[r]));
+        }
+        return;
+    }
     const bool ip = i + 1 < p.nx, jp = j + 1 < p.ny;
     T ex[kPZ + 1], ey[kPZ + 1];
     T ez[kPZ], ex_j[kPZ], ez_j[kPZ], ey_i[kPZ], ez_i[kPZ], hx[kPZ], hy[kPZ], hz[kPZ];
@@ -222,7 +277,50 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_EBG_MINB) e_bg_kernel(const KP
     const int bi0 = blockIdx.x * kBX, bj0 = blockIdx.y * kBY;
     const bool block_in_design = bi0 >= p.db[0] && bi0 + kBX <= p.db[1] && bj0 >= p.db[2] && bj0 + kBY <= p.db[3] &&
                                  k0 >= p.db[4] && k0 + kPZ <= p.db[5];
-    if (!block_in_design && i < p.nx && j < p.ny) {
+    if (!block_in_design && e_block_interior(p, bi0, bj0, k0)) {
+        if (i < p.nx && j < p.ny) {   // plain stencil, 32-bit indices
+            const T* __restrict__ Hx = p.H[0];
+            const T* __restrict__ Hy = p.H[1];
+            const T* __restrict__ Hz = p.H[2];
+            T* __restrict__ Ex = p.E[0];
+            T* __restrict__ Ey = p.E[1];
+            T* __restrict__ Ez = p.E[2];
+            const int nx = p.nx, pl = (int)p.plane;
+            const int id0 = (k0 * p.ny + j) * nx + i;
+            T fhx[kPZ + 1], fhy[kPZ + 1], fhz[kPZ], fhzj[kPZ], fhzi[kPZ], fhyi[kPZ], fhxj[kPZ], fe[kPZ][3];
+#pragma unroll
+            for (int r = 0; r <= kPZ; ++r) {
+                const int id = id0 + (r - 1) * pl;
+                fhx[r] = Hx[id];
+                fhy[r] = Hy[id];
+                if (r > 0) {
+                    const int q = r - 1;
+                    fhz[q] = Hz[id];
+                    fhzj[q] = Hz[id - nx];
+                    fhxj[q] = Hx[id - nx];
+                    fhzi[q] = Hz[id - 1];
+                    fhyi[q] = Hy[id - 1];
+                    fe[q][0] = Ex[id];
+                    fe[q][1] = Ey[id];
+                    fe[q][2] = Ez[id];
+                }
+            }
+            const T idx = p.inv_dx;
+            T emax = T(0);
+#pragma unroll
+            for (int r = 0; r < kPZ; ++r) {
+                const int id = id0 + r * pl;
+                const T ex = p.bg_ca[0] * fe[r][0] + p.bg_cb[0] * idx * ((fhz[r] - fhzj[r]) - (fhy[r + 1] - fhy[r]));
+                const T ey = p.bg_ca[1] * fe[r][1] + p.bg_cb[1] * idx * ((fhx[r + 1] - fhx[r]) - (fhz[r] - fhzi[r]));
+                const T ez = p.bg_ca[2] * fe[r][2] + p.bg_cb[2] * idx * ((fhy[r + 1] - fhyi[r]) - (fhx[r + 1] - fhxj[r]));
+                Ex[id] = ex;
+                Ey[id] = ey;
+                Ez[id] = ez;
+                emax = fmax(emax, fabs(ex) + fabs(ey) + fabs(ez));
+            }
+            if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
+        }
+    } else if (!block_in_design && i < p.nx && j < p.ny) {
         const T* __restrict__ Hx = p.H[0];
         const T* __restrict__ Hy = p.H[1];
         const T* __restrict__ Hz = p.H[2];

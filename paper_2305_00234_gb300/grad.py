@@ -42,6 +42,30 @@ class FdtdGrad(torch.autograd.Function):
         return g * grad_F.to(g.dtype), None
 
 
+class FilterProject(torch.autograd.Function):
+    """rho_b = FilterProject.apply(rho, R, beta, eta): cone filter (Eq. (FilterFunction)) and smoothed
+    Heaviside projection (Eq. (Projection)) on the GPU; backward is Eq. (GradientsFiltered)."""
+
+    @staticmethod
+    def forward(ctx, rho, R, beta, eta):
+        from . import _native as N
+        rho = rho.detach().contiguous().float()
+        rho_t, rho_b = torch.empty_like(rho), torch.empty_like(rho)
+        N.fdtd_filter_project(rho, rho_t, rho_b, R, beta, eta, torch.cuda.current_stream().cuda_stream)
+        ctx.save_for_backward(rho_t)
+        ctx.params = (R, beta, eta)
+        return rho_b
+
+    @staticmethod
+    def backward(ctx, g):
+        from . import _native as N
+        (rho_t,) = ctx.saved_tensors
+        out = torch.empty_like(rho_t)
+        N.fdtd_filter_project_grad(rho_t, g.contiguous().float(), out, *ctx.params,
+                                   torch.cuda.current_stream().cuda_stream)
+        return out, None, None, None
+
+
 def objective(rho, problem):
     """Differentiable F(rho)."""
     return FdtdGrad.apply(rho, problem)

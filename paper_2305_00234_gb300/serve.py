@@ -86,6 +86,7 @@ class GradientServer:
         self.active = 0
         self.closed = False
         self.peak_active = 0
+        self.peak_in_use = 0
         self.pool = cf.ThreadPoolExecutor(max_workers=max_slots)
         self.dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self.dispatcher.start()
@@ -123,6 +124,7 @@ class GradientServer:
                 self.in_use += fp
                 self.active += 1
                 self.peak_active = max(self.peak_active, self.active)
+                self.peak_in_use = max(self.peak_in_use, self.in_use)
             self.pool.submit(self._run, req, fp, fut, time.perf_counter())
 
     def _run(self, req, fp, fut, t_admit):
