@@ -38,7 +38,9 @@ def test_filter_project_and_chain_rule(N, shape, R, beta, eta):
     torch.cuda.synchronize()
     rt_o = OF.filter_density(rho.astype(np.float32).astype(np.float64), R)
     assert rel(rt.cpu().numpy(), rt_o) <= 1e-5
-    assert rel(rb.cpu().numpy(), OF.project(rt_o, beta, eta)) <= 1e-5
+    # the projection of the GPU's own filtered field (a steep projection amplifies the filter's
+    # FP32 rounding, which the line above already bounds)
+    assert rel(rb.cpu().numpy(), OF.project(rt.cpu().numpy().astype(np.float64), beta, eta)) <= 1e-5
     go = OF.chain_rule(g_b.astype(np.float32).astype(np.float64), rt.cpu().numpy().astype(np.float64), R, beta, eta)
     assert rel(grad.cpu().numpy(), go) <= 1e-5
 
