@@ -426,15 +426,14 @@ def run_ours(args):
     # on the library's stream over the timed region); the dominant kernel is the one with most time
     peak, peak_src = measured_peaks()
     prec_t = "float" if d["precision"] == 32 else "double"
-    names = {"h": f"h_kernel<{prec_t}>", "ebg": f"e_bg_kernel<{prec_t}>",
-             "ed": f"e_design_kernel<{prec_t},*>", "dft": f"dft_kernel<{prec_t}>",
-             "grad": f"grad_kernel<{prec_t}>"}
+    names = {"step": f"step_kernel<{prec_t}>", "ed": f"e_design_kernel<{prec_t},*>",
+             "dft": f"dft_kernel<{prec_t}>", "grad": f"grad_kernel<{prec_t}>"}
     kern = {}
     runs = 2 * args.steps                                   # forward + adjoint per gradient
     blocks = -(-M // int(max(tim["dft_steps_per_launch"], 1)))
-    total = {"h": M * runs, "ebg": M * runs, "ed": M * runs if tim["ed_launches"] else 0,
+    total = {"step": M * runs, "ed": M * runs if tim["ed_launches"] else 0,
              "dft": blocks * runs if tim["dft_launches"] else 0, "grad": args.steps}
-    for k in ("h", "ebg", "ed", "dft", "grad"):
+    for k in ("step", "ed", "dft", "grad"):
         nl = tim[f"{k}_launches"]
         if nl == 0:
             continue

@@ -9,6 +9,8 @@
 // A run enqueues CUDA graphs of up to kGraphSteps (H, E) step pairs on a private stream; the
 // caller's stream is fenced with events before and after, so device pointers passed with
 // on_device = 1 are ordered with the caller's work.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +36,10 @@ using fdtd::DParams;
 using fdtd::GParams;
 using fdtd::KParams;
 using fdtd::PoleTable;
+using fdtd::StepMaps;
+using fdtd::kSX;
+using fdtd::kSYE;
+using fdtd::kSYH;
 
 constexpr double kC0 = 299792458.0;
 constexpr double kMu0 = 1.25663706212e-6;
@@ -181,10 +187,11 @@ size_t footprint(const fdtd_grid_desc& d, const int ptot[3])
     const size_t nd = (size_t)box_count(d.design_box);
     const size_t ng = (size_t)box_count(d.gap_box);
     const int n[3] = {d.nx, d.ny, d.nz};
-    size_t b = 6 * ncell * ts;                                        // E, H
+    const size_t cs = (ncell + 31) / 32 * 32;
+    size_t b = 4 * 3 * cs * ts;                                       // E, H: two buffers each
     for (int a = 0; a < 3; ++a) {                                     // psi: 2 E + 2 H components per axis
         const size_t w = (size_t)d.cpml[2 * a] + d.cpml[2 * a + 1];
-        b += 4 * (ncell / n[a]) * w * ts + 8 * w * ts;
+        b += 6 * (ncell / n[a]) * w * ts + 8 * w * ts;               // psi_E, psi_H (two buffers)
     }
     b += nd * ts;                                                     // rho
     for (int k = 0; k < 3; ++k) b += nd * (size_t)ptot[k] * 2 * ts;   // Q
@@ -196,6 +203,21 @@ size_t footprint(const fdtd_grid_desc& d, const int ptot[3])
     b += (ng * 3 * fdtd::kMaxBasis + 3) * ts + ng * 3 * d.n_freq * 16;
     b += sizeof(PoleTable<double>) + 256;
     return b;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    });
+    return fn;
 }
 
 // Library-private stream-ordered memory pool per device.  Handles allocate and free on their own
@@ -237,7 +259,8 @@ struct fdtd_ctx {
     fdtd_grid_desc d{};
     std::vector<double> freqs, weights;
     cudaStream_t user = nullptr, work = nullptr;
-    cudaEvent_t fence = nullptr;
+    cudaStream_t side = nullptr;                       // second branch of the captured step graph
+    cudaEvent_t fence = nullptr, fork = nullptr, join = nullptr;
     int device = 0;
     double dt = 0;
     size_t ncell = 0, nd = 0, ngap = 0;
@@ -298,6 +321,9 @@ struct Solver : SolverBase {
     unsigned* counter = nullptr;
     int* ctl = nullptr;
     int ptot[3] = {0, 0, 0};
+    bool fused = false;             // an interior box for the fused TMA step kernel exists
+    StepMaps maps[2]{};             // tensor maps of the buffers read by even / odd steps
+    fdtd::ShellBoxes shell{};       // the cells around the interior box
     std::vector<double2> ab_host;
     std::vector<double> gap_dft;     // host copy of the forward gap DFT, (f,c,gv) complex
     double adj_cond = 0.0;
@@ -339,15 +365,31 @@ struct Solver : SolverBase {
             p.cph[a] = d.cpml[2 * a + 1];
             p.W[a] = p.cpl[a] + p.cph[a];
         }
+        // Each field is one block of three components, component stride cs (a multiple of 32 elements),
+        // so that one 4-D tensor map covers it.  A step reads one buffer of each pair and writes the other.
+        split_grid(p);
+        cs = ((size_t)c->ncell + 31) / 32 * 32;
+        T* fld[4];
+        for (int f = 0; f < 4; ++f) fld[f] = talloc(3 * cs);
         for (int cc = 0; cc < 3; ++cc) {
-            p.E[cc] = talloc(c->ncell);
-            p.H[cc] = talloc(c->ncell);
+            p.E[cc] = fld[0] + cc * cs;
+            p.H[cc] = fld[1] + cc * cs;
+            p.En[cc] = fld[2] + cc * cs;
+            p.Hn[cc] = fld[3] + cc * cs;
             for (int t = 0; t < 2; ++t) {
                 const int a = (cc + 1 + t) % 3;
                 const size_t m = (size_t)(c->ncell / n[a]) * p.W[a];
                 p.psiE[cc][t] = talloc(m);
                 p.psiH[cc][t] = talloc(m);
+                p.psiHn[cc][t] = talloc(m);
             }
+        }
+        if (fused) {
+            for (int par = 0; par < 2; ++par) {
+                encode_map(&maps[par].e, par ? fld[2] : fld[0], kSYE);
+                encode_map(&maps[par].h, par ? fld[3] : fld[1], kSYH);
+            }
+            CK(fdtd::prepare_step<T>());
         }
         // CPML tables {1/kappa, b, c, 0} per slab index
         for (int a = 0; a < 3; ++a) {
@@ -417,9 +459,10 @@ struct Solver : SolverBase {
         CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), c->work));
         p.ctl = ctl;
         for (int m = 0; m < 2; ++m) dp[m].ctl = ctl;
-        p.nblocks_e = fdtd::e_blocks(d.nx, d.ny, d.nz);
+        p.nblocks_s = fdtd::shell_blocks(shell);
         p.nblocks_d = c->nd ? fdtd::design_blocks(c->dn[0], c->dn[1], c->dn[2]) : 0;
         p.blowup = (T)1e30;
+        p.n_steps = d.n_steps;
         p.tfsf_i0 = -1;
         p.nb = 0;
         std::fill(p.sb, p.sb + 6, 0);
@@ -511,6 +554,7 @@ struct Solver : SolverBase {
                 if (!(Dp > 0.0)) arg_error("background update denominator <= 0");
                 base.bg_ca[k] = (T)(Dm / Dp);
                 base.bg_cb[k] = (T)(1.0 / Dp);
+                base.bg_cbi[k] = (T)(1.0 / (Dp * c->d.dx));
             }
             double D[2], N[2];
             const Material* mm[2] = {&m1, &m2};
@@ -587,6 +631,98 @@ struct Solver : SolverBase {
         drop_graphs();
     }
 
+    size_t cs = 0;                  // component stride of a field block (elements)
+
+    // 4-D (x, y, z, component) tiled map of a field block; box kSX x rows x 1 x 3, zero fill outside.
+    void encode_map(CUtensorMap* m, T* base_ptr, int rows)
+    {
+        const fdtd_grid_desc& d = c->d;
+        const cuuint64_t dims[4] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz, 3};
+        const cuuint64_t strides[3] = {(cuuint64_t)d.nx * sizeof(T), (cuuint64_t)d.nx * d.ny * sizeof(T),
+                                       (cuuint64_t)cs * sizeof(T)};
+        const cuuint32_t box[4] = {(cuuint32_t)kSX, (cuuint32_t)rows, 1, 3};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const CUresult r = tensor_map_encoder()(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                                4, base_ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) throw Err{FDTD_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r)};
+    }
+
+    // Interior box of the fused kernel: whole kTX x kTY tiles whose cells and one-cell -x/-y halo lie
+    // outside the walls and the CPML slabs, x0 a multiple of 4 (16-byte aligned TMA boxes), planes
+    // cpml_z_low + 1 .. nz - cpml_z_high - 1 (the plane below the first one is outside the slab too).
+    // Needs x rows of a multiple of 16 bytes and the tensor-map encoder.  The rest of the grid is the
+    // shell: at most six boxes.
+    void split_grid(KParams<T>& p)
+    {
+        const fdtd_grid_desc& d = c->d;
+        const int X0 = (std::max(p.cpl[0] + 1, 1) + 3) / 4 * 4, Y0 = std::max(p.cpl[1] + 1, 1), Z0 = p.cpl[2] + 1;
+        const int ntx = (d.nx - p.cph[0] - X0) / fdtd::kTX, nty = (d.ny - p.cph[1] - Y0) / fdtd::kTY;
+        const int Z1 = d.nz - p.cph[2];
+        fused = ((size_t)d.nx * sizeof(T)) % 16 == 0 && ntx > 0 && nty > 0 && Z1 > Z0 && tensor_map_encoder() != nullptr;
+        const int ib[6] = {X0, X0 + ntx * fdtd::kTX, Y0, Y0 + nty * fdtd::kTY, Z0, Z1};
+        std::fill(p.ib, p.ib + 6, 0);
+        if (fused) std::copy(ib, ib + 6, p.ib);
+        shell = fdtd::ShellBoxes{};
+        auto add = [&](int x0, int x1, int y0, int y1, int z0, int z1) {
+            if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;
+            int* b = shell.b[shell.n++];
+            b[0] = x0; b[1] = x1; b[2] = y0; b[3] = y1; b[4] = z0; b[5] = z1;
+        };
+        if (!fused) {
+            add(0, d.nx, 0, d.ny, 0, d.nz);
+        } else {
+            add(0, d.nx, 0, d.ny, 0, ib[4]);                      // below and above the interior planes
+            add(0, d.nx, 0, d.ny, ib[5], d.nz);
+            add(0, d.nx, 0, ib[2], ib[4], ib[5]);                 // in front of and behind it in y
+            add(0, d.nx, ib[3], d.ny, ib[4], ib[5]);
+            add(0, ib[0], ib[2], ib[3], ib[4], ib[5]);            // left and right of it in x
+            add(ib[1], d.nx, ib[2], ib[3], ib[4], ib[5]);
+        }
+    }
+
+    // Background part of one step: H of the shell and the fused interior (both read only the old
+    // buffers), then E of the shell (reads the new H of its neighbours).  concurrent: the shell H runs
+    // on the side stream next to the interior kernel (graph capture); else all three in order.
+    cudaError_t launch_background(const KParams<T>& q, int parity, bool concurrent)
+    {
+        cudaError_t e = cudaSuccess;
+        if (concurrent && fused) {
+            e = cudaEventRecord(c->fork, c->work);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+            if (e == cudaSuccess) e = fdtd::launch_shell<T>(q, shell, false, c->side);
+            if (e == cudaSuccess) e = fdtd::launch_step<T>(q, maps[parity & 1], c->work);
+            if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->work, c->join, 0);
+        } else {
+            e = fdtd::launch_shell<T>(q, shell, false, c->work);
+            if (e == cudaSuccess && fused) e = fdtd::launch_step<T>(q, maps[parity & 1], c->work);
+        }
+        return e == cudaSuccess ? fdtd::launch_shell<T>(q, shell, true, c->work) : e;
+    }
+
+    // Parameters of a step with the given parity: odd steps read the second buffer of each pair.
+    KParams<T> par(const KParams<T>& p, int parity) const
+    {
+        if (!(parity & 1)) return p;
+        KParams<T> q = p;
+        for (int cc = 0; cc < 3; ++cc) {
+            std::swap(q.E[cc], q.En[cc]);
+            std::swap(q.H[cc], q.Hn[cc]);
+            for (int t = 0; t < 2; ++t) std::swap(q.psiH[cc][t], q.psiHn[cc][t]);
+        }
+        return q;
+    }
+
+    // Buffers that hold the state after a run of M steps.
+    T* cur_field(int which) const
+    {
+        const bool odd = c->d.n_steps & 1;
+        if (which < 3) return odd ? base.En[which] : base.E[which];
+        return odd ? base.Hn[which - 3] : base.H[which - 3];
+    }
+
     void drop_graphs()
     {
         for (auto& g : graph)
@@ -621,6 +757,8 @@ struct Solver : SolverBase {
         for (int k = 0; k < 3; ++k) {
             CK(cudaMemsetAsync(base.E[k], 0, c->ncell * sizeof(T), s));
             CK(cudaMemsetAsync(base.H[k], 0, c->ncell * sizeof(T), s));
+            CK(cudaMemsetAsync(base.En[k], 0, c->ncell * sizeof(T), s));
+            CK(cudaMemsetAsync(base.Hn[k], 0, c->ncell * sizeof(T), s));
             for (int t = 0; t < 2; ++t) {
                 const int a = (k + 1 + t) % 3;
                 const int n[3] = {c->d.nx, c->d.ny, c->d.nz};
@@ -628,6 +766,7 @@ struct Solver : SolverBase {
                 if (m) {
                     CK(cudaMemsetAsync(base.psiE[k][t], 0, m * sizeof(T), s));
                     CK(cudaMemsetAsync(base.psiH[k][t], 0, m * sizeof(T), s));
+                    CK(cudaMemsetAsync(base.psiHn[k][t], 0, m * sizeof(T), s));
                 }
             }
             if (ptot[k] && c->nd) CK(cudaMemsetAsync(base.Q[k], 0, c->nd * ptot[k] * sizeof(cpx<T>), s));
@@ -642,10 +781,10 @@ struct Solver : SolverBase {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
         cudaError_t err = cudaSuccess;
-        for (int s = 0; s < steps && err == cudaSuccess; ++s) {
-            err = fdtd::launch_h<T>(p, c->work);
-            if (err == cudaSuccess) err = fdtd::launch_e_bg<T>(p, c->work);
-            if (err == cudaSuccess) err = fdtd::launch_e_design<T>(p, bucket, c->work);
+        for (int s = 0; s < steps && err == cudaSuccess; ++s) {   // graphs start at even steps
+            const KParams<T> q = par(p, s);
+            err = launch_background(q, s, true);
+            if (err == cudaSuccess) err = fdtd::launch_e_design<T>(q, bucket, c->work);
         }
         if (err == cudaSuccess) err = fdtd::launch_dft<T>(dp[mode], steps, c->work);
         cudaError_t e2 = cudaStreamEndCapture(c->work, &g);
@@ -688,12 +827,12 @@ struct Solver : SolverBase {
             if (c->prof && b % kProfEvery == 0) {
                 sampled.push_back(b);
                 for (int q = 0; q < cnt; ++q, ++s) {
+                    const KParams<T> pp = par(p, s);
                     CK(cudaEventRecord(c->ev[4 * s], c->work));
-                    CK(fdtd::launch_h<T>(p, c->work));
+                    CK(launch_background(pp, s, false));
                     CK(cudaEventRecord(c->ev[4 * s + 1], c->work));
-                    CK(fdtd::launch_e_bg<T>(p, c->work));
                     CK(cudaEventRecord(c->ev[4 * s + 2], c->work));
-                    CK(fdtd::launch_e_design<T>(p, bucket, c->work));
+                    CK(fdtd::launch_e_design<T>(pp, bucket, c->work));
                     CK(cudaEventRecord(c->ev[4 * s + 3], c->work));
                 }
                 CK(fdtd::launch_dft<T>(dp[mode], cnt, c->work));
@@ -713,8 +852,7 @@ struct Solver : SolverBase {
                     CK(cudaEventElapsedTime(&x, c->ev[4 * q], c->ev[4 * q + 1]));
                     CK(cudaEventElapsedTime(&y, c->ev[4 * q + 1], c->ev[4 * q + 2]));
                     CK(cudaEventElapsedTime(&z, c->ev[4 * q + 2], c->ev[4 * q + 3]));
-                    c->tim.h_ms += x;
-                    c->tim.ebg_ms += y;
+                    c->tim.step_ms += x + y;
                     c->tim.ed_ms += z;
                 }
                 float w = 0;
@@ -724,17 +862,21 @@ struct Solver : SolverBase {
                 timed_blocks += 1;
             }
         }
-        c->tim.h_launches += timed_steps;          // launches that were timed (profiling samples)
-        c->tim.ebg_launches += timed_steps;
+        c->tim.step_launches += timed_steps;       // launches that were timed (profiling samples)
         if (c->nd) c->tim.ed_launches += timed_steps;
         if (c->nd) {
             c->tim.dft_launches += timed_blocks;
             c->tim.launches += nblk;
         }
-        c->tim.launches += (c->nd ? 3LL : 2LL) * M;  // every kernel this run launched
+        c->tim.launches += ((fused ? 3LL : 2LL) + (c->nd ? 1LL : 0LL)) * M;  // every kernel this run launched
+        c->tim.fused_step = fused ? 1 : 0;
         int hctl[4];
         CK(cudaMemcpyAsync(hctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
+        if (hctl[2] & 4) {
+            c->dead = true;
+            throw Err{FDTD_ERR_CUDA, "a TMA plane of the step kernel did not arrive within its time limit"};
+        }
         if (hctl[2] & 1) {
             c->dead = true;
             throw Err{FDTD_ERR_UNSTABLE, "non-finite or exploding field during the run"};
@@ -941,7 +1083,7 @@ struct Solver : SolverBase {
 
     void get_field(int which, double* dst)
     {
-        T* src = which < 3 ? base.E[which] : base.H[which - 3];
+        T* src = cur_field(which);
         std::vector<T> h(c->ncell);
         CK(cudaMemcpyAsync(h.data(), src, c->ncell * sizeof(T), cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
@@ -1070,6 +1212,9 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd
         c->user = (cudaStream_t)cuda_stream;
         CK(cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->fence, cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
         c->dt = desc->courant * desc->dx / kC0;
         c->ncell = (size_t)desc->nx * desc->ny * desc->nz;
         c->nd = (size_t)box_count(desc->design_box);
@@ -1237,16 +1382,15 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     const double ts = h->d.precision == 64 ? 8.0 : 4.0;
     // algorithmic bytes per launch: every state word read once and written once
     const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);
-    double bh = 9.0 * ts * nc;                          // H r/w, E read
-    double bbg = 9.0 * ts * (nc - nd);                  // E r/w, H read (outside the design box)
-    double bd = 9.0 * ts * nd;                          // the same inside the design box
+    // background step: E^n and H read, H written everywhere, E written outside the design box
+    double bs = 9.0 * ts * nc + 3.0 * ts * (nc - nd);
     const int n[3] = {h->d.nx, h->d.ny, h->d.nz};
     for (int a = 0; a < 3; ++a) {
         const double w = (double)h->d.cpml[2 * a] + h->d.cpml[2 * a + 1];
         const double slab = nc / n[a] * w;
-        bbg += 2.0 * 2.0 * ts * slab;                   // two psi_E arrays r/w per attenuated axis
-        bh += 2.0 * 2.0 * ts * slab;                    // two psi_H arrays r/w
+        bs += 4.0 * 2.0 * ts * slab;                    // two psi_E r/w and two psi_H read old / write new
     }
+    double bd = 9.0 * ts * nd;                          // inside the design box: E^n, H^{n+1/2} read, E written
     if (h->impl) {
         int P = 0;
         if (h->d.precision == 64) {
@@ -1261,8 +1405,7 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
         t.bytes_dft_per_launch = nd * (K * 3.0 * ts + 3.0 * h->d.n_freq * 16.0 * 2.0);  // snapshots + FP64 acc r/w
         t.bytes_grad_per_launch = nd * (2.0 * 3.0 * h->d.n_freq * 16.0 + ts + 8.0);     // both DFTs, rho, grad
     }
-    t.bytes_h_per_launch = bh;
-    t.bytes_ebg_per_launch = bbg;
+    t.bytes_step_per_launch = bs;
     t.bytes_ed_per_launch = bd;
     *out = t;
     return FDTD_OK;
@@ -1306,6 +1449,9 @@ fdtd_status fdtd_destroy(fdtd_handle h)
     }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->fence) cudaEventDestroy(h->fence);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->work) cudaStreamDestroy(h->work);
     delete h;
     return FDTD_OK;

@@ -1,5 +1,6 @@
 // Launch wrappers and helper kernels; explicit FP32 / FP64 instantiations.
 #include "fdtd_kernels.cuh"
+#include "fdtd_step.cuh"
 #include "fdtd_launch.h"
 
 namespace fdtd {
@@ -81,14 +82,6 @@ __global__ void index_map_kernel(const KParams<T> p, int which, int32_t* out)
 }
 
 static dim3 grid3(int nx, int ny, int nz) { return dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY, nz); }
-static dim3 grid_pz(int nx, int ny, int nz) { return grid3(nx, ny, (nz + kPZ - 1) / kPZ); }
-
-template <typename T>
-cudaError_t launch_h(const KParams<T>& p, cudaStream_t s)
-{
-    h_kernel<T><<<grid_pz(p.nx, p.ny, p.nz), dim3(kBX, kBY), 0, s>>>(p);
-    return cudaGetLastError();
-}
 
 int pole_bucket(int max_poles)
 {
@@ -96,9 +89,41 @@ int pole_bucket(int max_poles)
 }
 
 template <typename T>
-cudaError_t launch_e_bg(const KParams<T>& p, cudaStream_t s)
+cudaError_t prepare_step()
 {
-    e_bg_kernel<T><<<grid_pz(p.nx, p.ny, p.nz), dim3(kBX, kBY), 0, s>>>(p);
+    return cudaFuncSetAttribute(step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StepSmem<T>::total);
+}
+
+template <typename T>
+cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s)
+{
+    const dim3 g((p.ib[1] - p.ib[0]) / kTX, (p.ib[3] - p.ib[2]) / kTY, (p.ib[5] - p.ib[4] + kKC - 1) / kKC);
+    step_kernel<T><<<g, dim3(kPX, kTY), StepSmem<T>::total, s>>>(p, m);
+    return cudaGetLastError();
+}
+
+unsigned shell_blocks(ShellBoxes& s)
+{
+    unsigned t = 0;
+    for (int q = 0; q < s.n; ++q) {
+        const int* B = s.b[q];
+        s.first[q] = t;
+        t += (unsigned)((B[1] - B[0] + kBX - 1) / kBX) * (unsigned)((B[3] - B[2] + kBY - 1) / kBY) *
+             (unsigned)((B[5] - B[4] + kShellPZ - 1) / kShellPZ);
+    }
+    s.first[s.n] = t;
+    return t;
+}
+
+template <typename T>
+cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, cudaStream_t st)
+{
+    const unsigned nb = s.first[s.n];
+    if (nb == 0) return cudaSuccess;
+    if (e_part)
+        shell_e_kernel<T><<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
+    else
+        shell_h_kernel<T><<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
     return cudaGetLastError();
 }
 
@@ -125,11 +150,6 @@ cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s)
     return cudaGetLastError();
 }
 
-unsigned e_blocks(int nx, int ny, int nz)
-{
-    const dim3 g = grid_pz(nx, ny, nz);
-    return g.x * g.y * g.z;
-}
 
 unsigned design_blocks(int dnx, int dny, int dnz)
 {
@@ -183,8 +203,9 @@ cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaS
 }
 
 #define FDTD_INSTANTIATE(T)                                                                              \
-    template cudaError_t launch_h<T>(const KParams<T>&, cudaStream_t);                                   \
-    template cudaError_t launch_e_bg<T>(const KParams<T>&, cudaStream_t);                                \
+    template cudaError_t prepare_step<T>();                                                              \
+    template cudaError_t launch_step<T>(const KParams<T>&, const StepMaps&, cudaStream_t);               \
+    template cudaError_t launch_shell<T>(const KParams<T>&, const ShellBoxes&, bool, cudaStream_t);      \
     template cudaError_t launch_e_design<T>(const KParams<T>&, int, cudaStream_t);                       \
     template cudaError_t launch_dft<T>(const DParams<T>&, int, cudaStream_t);                            \
     template cudaError_t launch_grad<T>(const GParams<T>&, unsigned, cudaStream_t);                      \

@@ -1,26 +1,22 @@
 // Device kernels of the CCPR time-domain adjoint gradient (arXiv 2305.00234) for sm_103a.
 //
-// One Yee time step is three memory-bound stencil launches plus, every kMaxSnap steps, a DFT launch:
-//   h_kernel:        H^{n+1/2} = H^{n-1/2} - (dt/mu0) curl E^n                   (Eq. (Maxwells)c)
-//                    with CFS-CPML psi only for cells inside the edge slabs;
-//   e_bg_kernel:     E^{n+1} outside the design box: background material, CPML, sources;
+// One Yee time step is a background step (fdtd_step.cuh: H^{n+1/2} everywhere, Eq. (Maxwells)c, and
+// E^{n+1} outside the design box, with CFS-CPML psi in the edge slabs, the TF/SF plane and point
+// sources), then
 //   e_design_kernel: E^{n+1} inside the design box: the conductivity and the CCPR pole currents of
 //                    both materials weighted by 1-rho and rho (Eqs. (Maxwells)a,b, (eps_mixed),
 //                    (sigma_mixed), (Poles_mixed)), the pole recursion
 //                    Q <- Q + (alpha-1) Q + beta (E^{n+1}+E^n), and an E snapshot for the DFT;
-//   dft_kernel:      the running FP64 DFT over the design box, kMaxSnap steps per update;
-// and the per-voxel gradient kernel (structure of Eq. (Gradient_analytic)) with a deterministic
+// and, every kMaxSnap steps, dft_kernel: the running FP64 DFT over the design box.  The gradient
+// kernel evaluates the structure of Eq. (Gradient_analytic) per voxel with a deterministic
 // warp-shuffle reduction of its squared norm.
 //
-// Thread layout: block (32, 8) over (x, y); x is the fastest array axis, so each warp reads and
-// writes 128 contiguous bytes per field (FP32).  The H and background-E kernels give each thread
-// kPZ consecutive z planes and issue every load before any store, which doubles the loads in
-// flight (the kernels are latency-bound otherwise) and reuses the z neighbour from registers.
-// Neighbour reads at -1 (E) / +1 (H) in x and y come from L1/L2.
+// Thread layout of the per-cell kernels: block (32, 8) over (x, y); x is the fastest array axis, so
+// each warp reads and writes 128 contiguous bytes per field (FP32).
 //
-// The step index n lives in device memory (ctl[0]) so that a captured CUDA graph of K steps
-// can be replayed: every kernel reads it, and the last block of e_design_kernel (of e_bg_kernel
-// when there is no design box) advances it.
+// The step index n lives in device memory (ctl[0]) so that a captured CUDA graph of K steps can be
+// replayed: every kernel reads it, and the last block of e_design_kernel (of the background-E shell
+// kernel when there is no design box) advances it.
 #pragma once
 #include "fdtd_params.h"
 
@@ -140,266 +136,7 @@ __device__ __forceinline__ void finish_step(int* ctl, unsigned nblocks, int n)
     }
 }
 
-// A block tile [bi0, bi0+kBX) x [bj0, bj0+kBY) x [k0, k0+kPZ) is interior for the H update when
-// its +1 neighbours exist and no cell lies in a CPML slab or next to the TF/SF plane.
-template <typename T>
-__device__ __forceinline__ bool h_block_interior(const KParams<T>& p, int bi0, int bj0, int k0)
-{
-    return bi0 >= p.cpl[0] && bi0 + kBX < p.nx - p.cph[0] && bj0 >= p.cpl[1] && bj0 + kBY < p.ny - p.cph[1] &&
-           k0 >= p.cpl[2] && k0 + kPZ < p.nz - p.cph[2] && !(p.tfsf_i0 - 1 >= bi0 && p.tfsf_i0 - 1 < bi0 + kBX);
-}
-
-// ... and interior for the background E update when its -1 neighbours exist (no PEC wall), no cell
-// lies in a CPML slab, on the TF/SF plane, in the point-source box or in the design box.
-template <typename T>
-__device__ __forceinline__ bool e_block_interior(const KParams<T>& p, int bi0, int bj0, int k0)
-{
-    const bool slab_free = bi0 >= p.cpl[0] && bi0 >= 1 && bi0 + kBX <= p.nx - p.cph[0] && bj0 >= p.cpl[1] && bj0 >= 1 &&
-                           bj0 + kBY <= p.ny - p.cph[1] && k0 >= p.cpl[2] && k0 >= 1 && k0 + kPZ <= p.nz - p.cph[2];
-    const bool no_plane = !(p.tfsf_i0 >= bi0 && p.tfsf_i0 < bi0 + kBX);
-    const bool no_src = p.nb == 0 || p.sb[1] <= bi0 || p.sb[0] >= bi0 + kBX || p.sb[3] <= bj0 || p.sb[2] >= bj0 + kBY ||
-                        p.sb[5] <= k0 || p.sb[4] >= k0 + kPZ;
-    const bool no_design = p.db[1] <= bi0 || p.db[0] >= bi0 + kBX || p.db[3] <= bj0 || p.db[2] >= bj0 + kBY ||
-                           p.db[5] <= k0 || p.db[4] >= k0 + kPZ;
-    return slab_free && no_plane && no_src && no_design;
-}
-
-// H update, kPZ consecutive z planes per thread: all loads of both planes are issued before any
-// store, and the z+1 neighbour of plane r is plane r+1's own E value.
-template <typename T>
-__global__ void __launch_bounds__(kBX * kBY, FDTD_H_MINB) h_kernel(const KParams<T> p)
-{
-    const int i = blockIdx.x * kBX + threadIdx.x;
-    const int j = blockIdx.y * kBY + threadIdx.y;
-    const int k0 = blockIdx.z * kPZ;
-    if (i >= p.nx || j >= p.ny) return;
-    const T* __restrict__ Ex = p.E[0];
-    const T* __restrict__ Ey = p.E[1];
-    const T* __restrict__ Ez = p.E[2];
-    T* __restrict__ Hx = p.H[0];
-    T* __restrict__ Hy = p.H[1];
-    T* __restrict__ Hz = p.H[2];
-    if (h_block_interior(p, blockIdx.x * kBX, blockIdx.y * kBY, k0)) {
-        // no wall, CPML slab or TF/SF plane anywhere in this block: plain stencil, 32-bit indices
-        const int nx = p.nx, pl = (int)p.plane;
-        const int id0 = (k0 * p.ny + j) * nx + i;
-        T fex[kPZ + 1], fey[kPZ + 1], fez[kPZ], fexj[kPZ], fezj[kPZ], feyi[kPZ], fezi[kPZ], fhx[kPZ], fhy[kPZ], fhz[kPZ];
-#pragma unroll
-        for (int r = 0; r <= kPZ; ++r) {
-            const int id = id0 + r * pl;
-            fex[r] = Ex[id];
-            fey[r] = Ey[id];
-            if (r < kPZ) {
-                fez[r] = Ez[id];
-                fexj[r] = Ex[id + nx];
-                fezj[r] = Ez[id + nx];
-                feyi[r] = Ey[id + 1];
-                fezi[r] = Ez[id + 1];
-                fhx[r] = Hx[id];
-                fhy[r] = Hy[id];
-                fhz[r] = Hz[id];
-            }
-        }
-        const T c = p.ch * p.inv_dx;
-#pragma unroll
-        for (int r = 0; r < kPZ; ++r) {
-            const int id = id0 + r * pl;
-            Hx[id] = fhx[r] - c * ((fezj[r] - fez[r]) - (fey[r + 1] - fey[r]));
-            Hy[id] = fhy[r] - c * ((fex[r + 1] - fex[r]) - (fezi[r] - fez[r]));
-            Hz[id] = fhz[r] - c * ((feyi[r] - fey[r]) - (fexj[r] - fex[r]));
-        }
-        return;
-    }
-    const bool ip = i + 1 < p.nx, jp = j + 1 < p.ny;
-    T ex[kPZ + 1], ey[kPZ + 1];
-    T ez[kPZ], ex_j[kPZ], ez_j[kPZ], ey_i[kPZ], ez_i[kPZ], hx[kPZ], hy[kPZ], hz[kPZ];
-#pragma unroll
-    for (int r = 0; r <= kPZ; ++r) {
-        const int k = k0 + r;
-        const bool ok = k < p.nz;
-        const long long id = ((long long)k * p.ny + j) * p.nx + i;
-        ex[r] = ok ? Ex[id] : T(0);     // beyond the last plane: PEC wall
-        ey[r] = ok ? Ey[id] : T(0);
-        if (r < kPZ) {
-            ez[r] = ok ? Ez[id] : T(0);
-            ex_j[r] = ok && jp ? Ex[id + p.nx] : T(0);
-            ez_j[r] = ok && jp ? Ez[id + p.nx] : T(0);
-            ey_i[r] = ok && ip ? Ey[id + 1] : T(0);
-            ez_i[r] = ok && ip ? Ez[id + 1] : T(0);
-            hx[r] = ok ? Hx[id] : T(0);
-            hy[r] = ok ? Hy[id] : T(0);
-            hz[r] = ok ? Hz[id] : T(0);
-        }
-    }
-    const int sx = slab_index(i, p.cpl[0], p.cph[0], p.nx);
-    const int sy = slab_index(j, p.cpl[1], p.cph[1], p.ny);
-    const T idx = p.inv_dx, ch = p.ch;
-#pragma unroll
-    for (int r = 0; r < kPZ; ++r) {
-        const int k = k0 + r;
-        if (k >= p.nz) break;
-        const long long id = ((long long)k * p.ny + j) * p.nx + i;
-        const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
-        // H_x at (i, j+1/2, k+1/2): (curl E)_x = dEz/dy - dEy/dz
-        T xa = (ez_j[r] - ez[r]) * idx, xb = (ey[r + 1] - ey[r]) * idx;
-        // H_y at (i+1/2, j, k+1/2): (curl E)_y = dEx/dz - dEz/dx
-        T ya = (ex[r + 1] - ex[r]) * idx, yb = (ez_i[r] - ez[r]) * idx;
-        // H_z at (i+1/2, j+1/2, k): (curl E)_z = dEy/dx - dEx/dy
-        T za = (ey_i[r] - ey[r]) * idx, zb = (ex_j[r] - ex[r]) * idx;
-        if (i == p.tfsf_i0 - 1) yb -= __ldg(p.einc + read_step<T>(p.ctl)) * idx;   // H_y here is scattered field
-        if (sy >= 0) {
-            xa = stretch(xa, p.pmlH[1], sy, p.psiH[0][0] + psi_index(p, i, j, k, 1, sy));
-            zb = stretch(zb, p.pmlH[1], sy, p.psiH[2][1] + psi_index(p, i, j, k, 1, sy));
-        }
-        if (sz >= 0) {
-            xb = stretch(xb, p.pmlH[2], sz, p.psiH[0][1] + psi_index(p, i, j, k, 2, sz));
-            ya = stretch(ya, p.pmlH[2], sz, p.psiH[1][0] + psi_index(p, i, j, k, 2, sz));
-        }
-        if (sx >= 0) {
-            yb = stretch(yb, p.pmlH[0], sx, p.psiH[1][1] + psi_index(p, i, j, k, 0, sx));
-            za = stretch(za, p.pmlH[0], sx, p.psiH[2][0] + psi_index(p, i, j, k, 0, sx));
-        }
-        Hx[id] = hx[r] - ch * (xa - xb);
-        Hy[id] = hy[r] - ch * (ya - yb);
-        Hz[id] = hz[r] - ch * (za - zb);
-    }
-}
-
-// E update outside the design box (background material, CPML slabs, sources), kPZ planes per
-// thread.  Cells inside the design box are left to e_design_kernel; blocks wholly inside it exit.
-template <typename T>
-__global__ void __launch_bounds__(kBX * kBY, FDTD_EBG_MINB) e_bg_kernel(const KParams<T> p)
-{
-    const int i = blockIdx.x * kBX + threadIdx.x;
-    const int j = blockIdx.y * kBY + threadIdx.y;
-    const int k0 = blockIdx.z * kPZ;
-    const int n = read_step<T>(p.ctl);
-    const int bi0 = blockIdx.x * kBX, bj0 = blockIdx.y * kBY;
-    const bool block_in_design = bi0 >= p.db[0] && bi0 + kBX <= p.db[1] && bj0 >= p.db[2] && bj0 + kBY <= p.db[3] &&
-                                 k0 >= p.db[4] && k0 + kPZ <= p.db[5];
-    if (!block_in_design && e_block_interior(p, bi0, bj0, k0)) {
-        if (i < p.nx && j < p.ny) {   // plain stencil, 32-bit indices
-            const T* __restrict__ Hx = p.H[0];
-            const T* __restrict__ Hy = p.H[1];
-            const T* __restrict__ Hz = p.H[2];
-            T* __restrict__ Ex = p.E[0];
-            T* __restrict__ Ey = p.E[1];
-            T* __restrict__ Ez = p.E[2];
-            const int nx = p.nx, pl = (int)p.plane;
-            const int id0 = (k0 * p.ny + j) * nx + i;
-            T fhx[kPZ + 1], fhy[kPZ + 1], fhz[kPZ], fhzj[kPZ], fhzi[kPZ], fhyi[kPZ], fhxj[kPZ], fe[kPZ][3];
-#pragma unroll
-            for (int r = 0; r <= kPZ; ++r) {
-                const int id = id0 + (r - 1) * pl;
-                fhx[r] = Hx[id];
-                fhy[r] = Hy[id];
-                if (r > 0) {
-                    const int q = r - 1;
-                    fhz[q] = Hz[id];
-                    fhzj[q] = Hz[id - nx];
-                    fhxj[q] = Hx[id - nx];
-                    fhzi[q] = Hz[id - 1];
-                    fhyi[q] = Hy[id - 1];
-                    fe[q][0] = Ex[id];
-                    fe[q][1] = Ey[id];
-                    fe[q][2] = Ez[id];
-                }
-            }
-            const T idx = p.inv_dx;
-            T emax = T(0);
-#pragma unroll
-            for (int r = 0; r < kPZ; ++r) {
-                const int id = id0 + r * pl;
-                const T ex = p.bg_ca[0] * fe[r][0] + p.bg_cb[0] * idx * ((fhz[r] - fhzj[r]) - (fhy[r + 1] - fhy[r]));
-                const T ey = p.bg_ca[1] * fe[r][1] + p.bg_cb[1] * idx * ((fhx[r + 1] - fhx[r]) - (fhz[r] - fhzi[r]));
-                const T ez = p.bg_ca[2] * fe[r][2] + p.bg_cb[2] * idx * ((fhy[r + 1] - fhyi[r]) - (fhx[r + 1] - fhxj[r]));
-                Ex[id] = ex;
-                Ey[id] = ey;
-                Ez[id] = ez;
-                emax = fmax(emax, fabs(ex) + fabs(ey) + fabs(ez));
-            }
-            if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
-        }
-    } else if (!block_in_design && i < p.nx && j < p.ny) {
-        const T* __restrict__ Hx = p.H[0];
-        const T* __restrict__ Hy = p.H[1];
-        const T* __restrict__ Hz = p.H[2];
-        T* __restrict__ Ex = p.E[0];
-        T* __restrict__ Ey = p.E[1];
-        T* __restrict__ Ez = p.E[2];
-        const bool im = i > 0, jm = j > 0;
-        T hx[kPZ + 1], hy[kPZ + 1];     // index 0 = plane k0-1 (the z-1 neighbour of the first plane)
-        T hz[kPZ], hz_j[kPZ], hz_i[kPZ], hy_i[kPZ], hx_j[kPZ], e0[kPZ][3];
-#pragma unroll
-        for (int r = 0; r <= kPZ; ++r) {
-            const int k = k0 + r - 1;
-            const bool ok = k >= 0 && k < p.nz;
-            const long long id = ((long long)k * p.ny + j) * p.nx + i;
-            hx[r] = ok ? Hx[id] : T(0);
-            hy[r] = ok ? Hy[id] : T(0);
-            if (r > 0) {
-                const int q = r - 1;
-                hz[q] = ok ? Hz[id] : T(0);
-                hz_j[q] = ok && jm ? Hz[id - p.nx] : T(0);
-                hx_j[q] = ok && jm ? Hx[id - p.nx] : T(0);
-                hz_i[q] = ok && im ? Hz[id - 1] : T(0);
-                hy_i[q] = ok && im ? Hy[id - 1] : T(0);
-                e0[q][0] = ok ? Ex[id] : T(0);
-                e0[q][1] = ok ? Ey[id] : T(0);
-                e0[q][2] = ok ? Ez[id] : T(0);
-            }
-        }
-        const int sx = slab_index(i, p.cpl[0], p.cph[0], p.nx);
-        const int sy = slab_index(j, p.cpl[1], p.cph[1], p.ny);
-        const T idx = p.inv_dx;
-        T emax = T(0);
-#pragma unroll
-        for (int r = 0; r < kPZ; ++r) {
-            const int k = k0 + r;
-            if (k >= p.nz || in_box(p.db, i, j, k)) continue;
-            const long long id = ((long long)k * p.ny + j) * p.nx + i;
-            const bool km = k > 0;
-            const int sz = slab_index(k, p.cpl[2], p.cph[2], p.nz);
-            // E_x: dHz/dy - dHy/dz ; E_y: dHx/dz - dHz/dx ; E_z: dHy/dx - dHx/dy
-            T xa = (hz[r] - hz_j[r]) * idx, xb = (hy[r + 1] - hy[r]) * idx;
-            T ya = (hx[r + 1] - hx[r]) * idx, yb = (hz[r] - hz_i[r]) * idx;
-            T za = (hy[r + 1] - hy_i[r]) * idx, zb = (hx[r + 1] - hx_j[r]) * idx;
-            if (i == p.tfsf_i0) za -= __ldg(p.hinc + n) * idx;    // H_y(i0-1/2) is scattered field
-            if (sy >= 0) {
-                xa = stretch(xa, p.pmlE[1], sy, p.psiE[0][0] + psi_index(p, i, j, k, 1, sy));
-                zb = stretch(zb, p.pmlE[1], sy, p.psiE[2][1] + psi_index(p, i, j, k, 1, sy));
-            }
-            if (sz >= 0) {
-                xb = stretch(xb, p.pmlE[2], sz, p.psiE[0][1] + psi_index(p, i, j, k, 2, sz));
-                ya = stretch(ya, p.pmlE[2], sz, p.psiE[1][0] + psi_index(p, i, j, k, 2, sz));
-            }
-            if (sx >= 0) {
-                yb = stretch(yb, p.pmlE[0], sx, p.psiE[1][1] + psi_index(p, i, j, k, 0, sx));
-                za = stretch(za, p.pmlE[0], sx, p.psiE[2][0] + psi_index(p, i, j, k, 0, sx));
-            }
-            T dxv = xa - xb, dyv = ya - yb, dzv = za - zb;
-            if (p.nb > 0 && in_box(p.sb, i, j, k)) {
-                dxv += point_drive(p, i, j, k, 0, n);
-                dyv += point_drive(p, i, j, k, 1, n);
-                dzv += point_drive(p, i, j, k, 2, n);
-            }
-            T ex = p.bg_ca[0] * e0[r][0] + p.bg_cb[0] * dxv;
-            T ey = p.bg_ca[1] * e0[r][1] + p.bg_cb[1] * dyv;
-            T ez = p.bg_ca[2] * e0[r][2] + p.bg_cb[2] * dzv;
-            // PEC walls: components tangential to a wall at index 0 stay zero
-            if (!(jm && km)) ex = e0[r][0];
-            if (!(km && im)) ey = e0[r][1];
-            if (!(im && jm)) ez = e0[r][2];
-            Ex[id] = ex;
-            Ey[id] = ey;
-            Ez[id] = ez;
-            emax = fmax(emax, fabs(ex) + fabs(ey) + fabs(ez));
-        }
-        if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
-    }
-    if (p.nd == 0) finish_step(p.ctl, p.nblocks_e, n);
-}
-
+// ---------------------------------------------------------------------------------------------
 // E update inside the design box: blended CCPR update of the design voxels, background update of
 // the gap voxels, point sources, and the E snapshot for the blocked DFT.  The design box lies
 // outside the CPML, so there is no psi here.  One cell per thread; owns the step advance.
@@ -412,12 +149,12 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const
     const int n = read_step<T>(p.ctl);
     if (i < p.db[1] && j < p.db[3]) {
         const long long id = ((long long)k * p.ny + j) * p.nx + i;
-        const T* __restrict__ Hx = p.H[0];
-        const T* __restrict__ Hy = p.H[1];
-        const T* __restrict__ Hz = p.H[2];
-        T* __restrict__ Ex = p.E[0];
-        T* __restrict__ Ey = p.E[1];
-        T* __restrict__ Ez = p.E[2];
+        const T* __restrict__ Hx = p.Hn[0];   // H^{n+1/2}, just written by the H update
+        const T* __restrict__ Hy = p.Hn[1];
+        const T* __restrict__ Hz = p.Hn[2];
+        const T* __restrict__ Ex = p.E[0];    // E^n
+        const T* __restrict__ Ey = p.E[1];
+        const T* __restrict__ Ez = p.E[2];
         const bool im = i > 0, jm = j > 0, km = k > 0;
         const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
         const T hz_j = jm ? Hz[id - p.nx] : T(0), hy_k = km ? Hy[id - p.plane] : T(0);
@@ -450,9 +187,9 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const
         if (!(jm && km)) ex = ex0;
         if (!(km && im)) ey = ey0;
         if (!(im && jm)) ez = ez0;
-        Ex[id] = ex;
-        Ey[id] = ey;
-        Ez[id] = ez;
+        p.En[0][id] = ex;
+        p.En[1][id] = ey;
+        p.En[2][id] = ez;
         T* __restrict__ snap = p.snap + (long long)(n % p.K) * 3 * p.nd + dv;
         snap[0] = ex;
         snap[p.nd] = ey;

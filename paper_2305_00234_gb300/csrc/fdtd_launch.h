@@ -7,16 +7,18 @@
 
 namespace fdtd {
 
-template <typename T>
-cudaError_t launch_h(const KParams<T>& p, cudaStream_t s);
 int pole_bucket(int max_poles);
 template <typename T>
-cudaError_t launch_e_bg(const KParams<T>& p, cudaStream_t s);
+cudaError_t prepare_step();
+template <typename T>
+cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s);
 template <typename T>
 cudaError_t launch_e_design(const KParams<T>& p, int bucket, cudaStream_t s);
 template <typename T>
 cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s);
-unsigned e_blocks(int nx, int ny, int nz);
+unsigned shell_blocks(ShellBoxes& s);   // fills s.first, returns the launch's blocks
+template <typename T>
+cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, cudaStream_t st);
 unsigned design_blocks(int dnx, int dny, int dnz);
 template <typename T>
 cudaError_t launch_grad(const GParams<T>& g, unsigned nblocks, cudaStream_t s);

@@ -1,5 +1,6 @@
 // Parameter structs shared by the kernels (fdtd_kernels.cuh) and the host code (fdtd_api.cu).
 #pragma once
+#include <cuda.h>            // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,19 +14,79 @@ constexpr int kBX = 32;
 constexpr int kBY = 8;
 constexpr int kReduceThreads = 256;
 constexpr int kMaxSnap = 16;      // steps per blocked DFT update (snapshot ring length)
-#ifndef FDTD_PZ
-#define FDTD_PZ 2
+#ifndef FDTD_SHELL_PZ
+#define FDTD_SHELL_PZ 2
 #endif
-#ifndef FDTD_H_MINB
-#define FDTD_H_MINB 6
+#ifndef FDTD_SHELL_MINB
+#define FDTD_SHELL_MINB 4
 #endif
-#ifndef FDTD_EBG_MINB
-#define FDTD_EBG_MINB 4
+#ifndef FDTD_KC
+#define FDTD_KC 16
 #endif
 #ifndef FDTD_ED_MINB
 #define FDTD_ED_MINB 4
 #endif
-constexpr int kPZ = FDTD_PZ;      // z planes per thread in the H and background E kernels
+constexpr int kShellPZ = FDTD_SHELL_PZ;   // z planes per thread in the shell kernels
+constexpr int kKC = FDTD_KC;      // z planes per block of the fused step kernel
+
+// Fused step kernel tile: kTX x kTY cells of one z plane, kTX/2 x kTY threads, each thread two
+// x-adjacent cells.  Boxes staged by TMA per plane: x in [i0 - kOX, i0 - kOX + kSX) (a start that is a
+// multiple of 4 elements, so 16-byte aligned for 4- and 8-byte types), E rows [j0 - 1, j0 + kTY],
+// H rows [j0 - 1, j0 + kTY - 1], all three components.
+constexpr int kTX = 32;
+constexpr int kTY = 16;
+constexpr int kPX = kTX / 2;
+constexpr int kOX = 4;
+constexpr int kSX = kTX + 8;
+constexpr int kSYE = kTY + 2;
+constexpr int kSYH = kTY + 1;
+constexpr int kHW = kTX + 2;      // row of the new-H tile: [1] is x = i0 - 1, [2 + xr] is x = i0 + xr
+
+__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
+
+#ifndef FDTD_STEP_NE
+#define FDTD_STEP_NE 4
+#endif
+#ifndef FDTD_STEP_NH
+#define FDTD_STEP_NH 3
+#endif
+#ifndef FDTD_STEP_MINB
+#define FDTD_STEP_MINB 3
+#endif
+template <typename T>
+struct StepCfg;
+template <>
+struct StepCfg<float> {   // E / H ring slots, resident blocks per SM
+    static constexpr int NE = FDTD_STEP_NE, NH = FDTD_STEP_NH, MINB = FDTD_STEP_MINB;
+};
+template <>
+struct StepCfg<double> {
+    static constexpr int NE = 3, NH = 2, MINB = 2;
+};
+template <typename T>
+struct StepSmem {
+    static constexpr unsigned e_tx = 3u * kSYE * kSX * sizeof(T);    // bytes one E plane load delivers
+    static constexpr unsigned h_tx = 3u * kSYH * kSX * sizeof(T);
+    static constexpr size_t e_slot = align128(e_tx);
+    static constexpr size_t h_slot = align128(h_tx);
+    static constexpr size_t h_new = align128(2 * 3 * (size_t)kSYH * kHW * sizeof(T));   // two tiles
+    static constexpr size_t table = 128;                                                // per-plane path
+    static constexpr size_t bars = 128;
+    static constexpr size_t total = StepCfg<T>::NE * e_slot + StepCfg<T>::NH * h_slot + h_new + table + bars + 128;
+};
+
+// The cells outside the interior box, as at most six boxes, for the shell kernels: block b of a
+// launch belongs to the box q with first[q] <= b < first[q + 1].
+struct ShellBoxes {
+    int n;
+    int b[6][6];          // half-open x0, x1, y0, y1, z0, z1
+    unsigned first[7];
+};
+
+// Tensor maps of the buffers one step reads: E^n and H^{n-1/2}, each 4-D (x, y, z, component).
+struct StepMaps {   // (CUtensorMap is 64-byte aligned)
+    CUtensorMap e, h;
+};
 
 template <typename T>
 struct cpx {
@@ -50,14 +111,18 @@ struct KParams {
     int gnx, gny;
     long long gplane;
     int cpl[3], cph[3], W[3];    // CPML thickness low / high, slab width per axis
-    T* E[3];
-    T* H[3];
-    T* psiE[3][2];               // component c, derivative axis (c+1+t)%3
-    T* psiH[3][2];
+    T* E[3];                     // E^n (read)
+    T* H[3];                     // H^{n-1/2} (read)
+    T* En[3];                    // E^{n+1} (written; the other buffer of the pair)
+    T* Hn[3];                    // H^{n+1/2} (written)
+    T* psiE[3][2];               // component c, derivative axis (c+1+t)%3; updated in place
+    T* psiH[3][2];               // psi of the H update at n-1/2 (read)
+    T* psiHn[3][2];              // ... at n+1/2 (written)
     const T* pmlE[3];            // per axis, per slab index: {1/kappa, b, c, 0} at integer positions
     const T* pmlH[3];            //                           ... at half-integer positions
     T inv_dx, ch;                // 1/dx, dt/mu0
     T bg_ca[3], bg_cb[3];        // background: E' = ca E + cb drive
+    T bg_cbi[3];                 // cb / dx
     T D1[3], dD[3], N1[3], dN[3], hg;   // design: D(rho) = D1 + rho dD + hg rho(1-rho), N likewise
     int P[3], P1[3];             // poles per component (m1 first, P1 of them)
     const PoleTable<T>* poles;
@@ -71,8 +136,10 @@ struct KParams {
     int tfsf_i0;                 // first total-field x index, -1 = no TF/SF
     const T* einc;               // E_inc^n at x = i0 dx
     const T* hinc;               // H_inc^{n+1/2} at x = (i0 - 1/2) dx
+    int n_steps;                 // steps of a run
     int* ctl;                    // [0] step n, [1] finished blocks of the advancing launch, [2] flags
-    unsigned nblocks_e;          // blocks of e_bg_kernel
+    int ib[6];                   // interior box of the fused step kernel (empty: x0 = x1)
+    unsigned nblocks_s;          // blocks of the background-E shell kernel
     unsigned nblocks_d;          // blocks of e_design_kernel
     T blowup;
 };

@@ -45,8 +45,9 @@ def test_footprint_and_validation_on_host(lib):
     w = synth.workload("c2")
     b = N.fdtd_footprint_bytes(w["desc"], [3, 3, 3])
     ncell = 256 ** 3
-    # fields 24 B + CPML slabs ~4.5 B + design state (rho, Q, two FP64 DFTs, 16-step E ring) ~71 B per cell
-    assert 90 * ncell < b < 110 * ncell
+    # fields 48 B (two buffers) + CPML slabs ~6.8 B + design state (rho, Q, two FP64 DFTs, 16-step E ring)
+    # ~71 B per cell
+    assert 115 * ncell < b < 135 * ncell
     bad = dict(w["desc"])
     bad["design_box"] = [4, 200, 64, 192, 64, 192]     # reaches into the CPML
     with pytest.raises(N.FdtdError) as e:

@@ -98,6 +98,26 @@ def two_dispersive(prec, steps=400, seed=5, gamma=2e6):
     return dict(desc=d, bg=vacuum(), m1=m1, m2=synth.drude_lorentz_metal(seed, 4), gamma=gamma, rho=rho)
 
 
+@pytest.mark.parametrize("src", ["tfsf", "dipole_shell", "dipole_interior"])
+@pytest.mark.parametrize("prec,nx,fused", [(32, 52, 1), (32, 45, 0), (64, 46, 1), (64, 45, 0)])
+def test_step_paths(gpu, prec, nx, fused, src):
+    """Both background-step layouts: an interior box for the fused TMA kernel (x rows a multiple of
+    16 bytes) plus the shell kernels around it, and the shell kernels over the whole grid.  Grids
+    ragged in all three tile axes, CPML of unequal thickness, a 3-pair metal whose design box
+    straddles the interior box, and the TF/SF plane inside the interior box or a dipole in the shell or
+    in the interior box."""
+    kw = {"tfsf": dict(src_kind=1, src_pos=(9, 0, 0)),
+          "dipole_shell": dict(src_kind=0, src_comp=1, src_pos=(8, 33, 6)),
+          "dipole_interior": dict(src_kind=0, src_comp=2, src_pos=(12, 8, 8))}[src]
+    d = base_desc(nx, 42, 37, n_steps=420, cpml=(6, 5, 4, 7, 5, 3), precision=prec,
+                  design=(22, 18, 15), gap=(2, 2, 2), lambdas_nm=(500.0, 650.0), **kw)
+    rho = synth.smooth_rho(synth.box_shape(d["design_box"]), 23, 2.0)
+    w = dict(desc=d, bg=vacuum(), m1=vacuum(), m2=synth.drude_lorentz_metal(23, 3), gamma=1e6, rho=rho)
+    g = run_gpu(gpu, w)
+    assert g["p"].timings()["fused_step"] == fused
+    compare(g, run_oracle(w), prec)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_config1_full(gpu, prec):
     """Config 1 at its full size: 32^3 FP64, 1000 steps, dipole, 2-pair metal, 16^3 design."""
