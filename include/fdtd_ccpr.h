@@ -104,17 +104,19 @@ typedef struct {
  * the others as CUDA graphs.  *_ms sum and *_launches count those timed launches (grad: every
  * launch); launches counts every kernel this library launched since the last reset. */
 typedef struct {
-    /* summed device time per kernel kind: background step (H everywhere + E outside the design box:
-     * one fused kernel, or the separate H and E kernels), E update inside the design box, blocked
-     * DFT, gradient */
-    double step_ms, ed_ms, dft_ms, grad_ms;
-    long long step_launches, ed_launches, dft_launches, grad_launches;
+    /* summed device time per kernel: the background step's shell H update, fused interior update and
+     * shell E update (one launch each per step), the E update inside the design box, the blocked
+     * DFT, the gradient */
+    double shell_h_ms, step_ms, shell_e_ms, ed_ms, dft_ms, grad_ms;
+    long long shell_h_launches, step_launches, shell_e_launches, ed_launches, dft_launches, grad_launches;
     long long launches;                      /* every kernel launch of this library */
-    /* algorithmic bytes per launch: each state word read once and written once */
-    double bytes_step_per_launch, bytes_ed_per_launch, bytes_dft_per_launch, bytes_grad_per_launch;
+    /* algorithmic bytes per launch: each word the kernel must move, read once and written once */
+    double bytes_shell_h_per_launch, bytes_step_per_launch, bytes_shell_e_per_launch, bytes_ed_per_launch,
+        bytes_dft_per_launch, bytes_grad_per_launch;
     double dft_steps_per_launch;             /* time steps folded into one DFT launch */
-    long long fused_step;                    /* 1: the last run used the fused TMA step kernel (grids whose
-                                                x row is a multiple of 16 bytes); 0: separate H and E kernels */
+    long long fused_step;                    /* 1: the grid has an interior box for the fused TMA kernel
+                                                (x rows a multiple of 16 bytes, room inside the CPML);
+                                                0: the shell kernels cover the whole grid */
 } fdtd_timings;
 
 /* Create a problem on the given CUDA stream (cudaStream_t; NULL = default stream) of the current

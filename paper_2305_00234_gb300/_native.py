@@ -46,10 +46,11 @@ class Material(C.Structure):
 
 
 class Timings(C.Structure):
-    _fields_ = [(k, C.c_double) for k in ("step_ms", "ed_ms", "dft_ms", "grad_ms")] + \
-               [(k, C.c_longlong) for k in ("step_launches", "ed_launches", "dft_launches", "grad_launches",
-                                            "launches")] + \
-               [(k, C.c_double) for k in ("bytes_step_per_launch", "bytes_ed_per_launch", "bytes_dft_per_launch",
+    _fields_ = [(k, C.c_double) for k in ("shell_h_ms", "step_ms", "shell_e_ms", "ed_ms", "dft_ms", "grad_ms")] + \
+               [(k, C.c_longlong) for k in ("shell_h_launches", "step_launches", "shell_e_launches", "ed_launches",
+                                            "dft_launches", "grad_launches", "launches")] + \
+               [(k, C.c_double) for k in ("bytes_shell_h_per_launch", "bytes_step_per_launch",
+                                          "bytes_shell_e_per_launch", "bytes_ed_per_launch", "bytes_dft_per_launch",
                                           "bytes_grad_per_launch", "dft_steps_per_launch")] + \
                [("fused_step", C.c_longlong)]
 

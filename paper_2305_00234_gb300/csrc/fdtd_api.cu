@@ -253,6 +253,7 @@ cudaMemPool_t device_pool(int device)
 // ---------------------------------------------------------------------------------------------
 struct SolverBase {
     virtual ~SolverBase() = default;
+    virtual void interior_box(int ib[6]) const = 0;
 };
 
 struct fdtd_ctx {
@@ -330,6 +331,7 @@ struct Solver : SolverBase {
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [mode][full, remainder]
 
     explicit Solver(fdtd_ctx* ctx) : c(ctx) {}
+    void interior_box(int ib[6]) const override { std::copy(base.ib, base.ib + 6, ib); }
     ~Solver() override
     {
         for (auto& g : graph)
@@ -814,7 +816,7 @@ struct Solver : SolverBase {
         int timed_steps = 0, timed_blocks = 0;
         std::vector<int> sampled;
         if (c->prof) {
-            const size_t need = 4 * (size_t)M + nblk;
+            const size_t need = 5 * (size_t)M + nblk;
             while (c->ev.size() < need) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
@@ -828,15 +830,19 @@ struct Solver : SolverBase {
                 sampled.push_back(b);
                 for (int q = 0; q < cnt; ++q, ++s) {
                     const KParams<T> pp = par(p, s);
-                    CK(cudaEventRecord(c->ev[4 * s], c->work));
-                    CK(launch_background(pp, s, false));
-                    CK(cudaEventRecord(c->ev[4 * s + 1], c->work));
-                    CK(cudaEventRecord(c->ev[4 * s + 2], c->work));
+                    cudaEvent_t* e = &c->ev[5 * (size_t)s];
+                    CK(cudaEventRecord(e[0], c->work));
+                    CK(fdtd::launch_shell<T>(pp, shell, false, c->work));
+                    CK(cudaEventRecord(e[1], c->work));
+                    if (fused) CK(fdtd::launch_step<T>(pp, maps[s & 1], c->work));
+                    CK(cudaEventRecord(e[2], c->work));
+                    CK(fdtd::launch_shell<T>(pp, shell, true, c->work));
+                    CK(cudaEventRecord(e[3], c->work));
                     CK(fdtd::launch_e_design<T>(pp, bucket, c->work));
-                    CK(cudaEventRecord(c->ev[4 * s + 3], c->work));
+                    CK(cudaEventRecord(e[4], c->work));
                 }
                 CK(fdtd::launch_dft<T>(dp[mode], cnt, c->work));
-                CK(cudaEventRecord(c->ev[4 * (size_t)M + b], c->work));
+                CK(cudaEventRecord(c->ev[5 * (size_t)M + b], c->work));
             } else {
                 CK(cudaGraphLaunch(graph[mode][b < full ? 0 : 1], c->work));
                 s += cnt;
@@ -848,21 +854,23 @@ struct Solver : SolverBase {
             for (int b : sampled) {
                 const int first = b * K, cnt = std::min(K, M - b * K);
                 for (int q = first; q < first + cnt; ++q) {
-                    float x = 0, y = 0, z = 0;
-                    CK(cudaEventElapsedTime(&x, c->ev[4 * q], c->ev[4 * q + 1]));
-                    CK(cudaEventElapsedTime(&y, c->ev[4 * q + 1], c->ev[4 * q + 2]));
-                    CK(cudaEventElapsedTime(&z, c->ev[4 * q + 2], c->ev[4 * q + 3]));
-                    c->tim.step_ms += x + y;
-                    c->tim.ed_ms += z;
+                    float t[4] = {0, 0, 0, 0};
+                    for (int u = 0; u < 4; ++u) CK(cudaEventElapsedTime(&t[u], c->ev[5 * (size_t)q + u], c->ev[5 * (size_t)q + u + 1]));
+                    c->tim.shell_h_ms += t[0];
+                    c->tim.step_ms += t[1];
+                    c->tim.shell_e_ms += t[2];
+                    c->tim.ed_ms += t[3];
                 }
                 float w = 0;
-                CK(cudaEventElapsedTime(&w, c->ev[4 * (first + cnt - 1) + 3], c->ev[4 * (size_t)M + b]));
+                CK(cudaEventElapsedTime(&w, c->ev[5 * (size_t)(first + cnt - 1) + 4], c->ev[5 * (size_t)M + b]));
                 c->tim.dft_ms += w;
                 timed_steps += cnt;
                 timed_blocks += 1;
             }
         }
-        c->tim.step_launches += timed_steps;       // launches that were timed (profiling samples)
+        c->tim.shell_h_launches += timed_steps;    // launches that were timed (profiling samples)
+        c->tim.shell_e_launches += timed_steps;
+        if (fused) c->tim.step_launches += timed_steps;
         if (c->nd) c->tim.ed_launches += timed_steps;
         if (c->nd) {
             c->tim.dft_launches += timed_blocks;
@@ -1382,13 +1390,29 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     const double ts = h->d.precision == 64 ? 8.0 : 4.0;
     // algorithmic bytes per launch: every state word read once and written once
     const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);
-    // background step: E^n and H read, H written everywhere, E written outside the design box
-    double bs = 9.0 * ts * nc + 3.0 * ts * (nc - nd);
+    // interior (fused) kernel: E^n and H read, H written, E written outside the design box;
+    // shell kernels: H: E^n, H read, H written; E: H, E^n read, E written (outside the design box);
+    // psi: per CPML slab cell and axis two psi_H read and written (H kernel), two psi_E (E kernel)
+    double bst = 0.0, bsh = 0.0, bse = 0.0;
+    if (h->impl) {
+        int ib[6];
+        h->impl->interior_box(ib);
+        const double ni = (double)(ib[1] - ib[0]) * (ib[3] - ib[2]) * (ib[5] - ib[4]);
+        const int* db = h->d.design_box;
+        double ndi = 1.0;
+        for (int a = 0; a < 3; ++a)
+            ndi *= std::max(0, std::min(ib[2 * a + 1], db[2 * a + 1]) - std::max(ib[2 * a], db[2 * a]));
+        if (box_count(db) == 0) ndi = 0.0;
+        bst = 12.0 * ts * ni - 3.0 * ts * ndi;
+        bsh = 9.0 * ts * (nc - ni);
+        bse = 9.0 * ts * ((nc - ni) - (nd - ndi));
+    }
     const int n[3] = {h->d.nx, h->d.ny, h->d.nz};
     for (int a = 0; a < 3; ++a) {
         const double w = (double)h->d.cpml[2 * a] + h->d.cpml[2 * a + 1];
         const double slab = nc / n[a] * w;
-        bs += 4.0 * 2.0 * ts * slab;                    // two psi_E r/w and two psi_H read old / write new
+        bsh += 4.0 * ts * slab;
+        bse += 4.0 * ts * slab;
     }
     double bd = 9.0 * ts * nd;                          // inside the design box: E^n, H^{n+1/2} read, E written
     if (h->impl) {
@@ -1405,7 +1429,9 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
         t.bytes_dft_per_launch = nd * (K * 3.0 * ts + 3.0 * h->d.n_freq * 16.0 * 2.0);  // snapshots + FP64 acc r/w
         t.bytes_grad_per_launch = nd * (2.0 * 3.0 * h->d.n_freq * 16.0 + ts + 8.0);     // both DFTs, rho, grad
     }
-    t.bytes_step_per_launch = bs;
+    t.bytes_shell_h_per_launch = bsh;
+    t.bytes_step_per_launch = bst;
+    t.bytes_shell_e_per_launch = bse;
     t.bytes_ed_per_launch = bd;
     *out = t;
     return FDTD_OK;
