@@ -53,6 +53,8 @@ def load():
     lib.oracle_forward.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
     lib.oracle_adjoint.argtypes = [C.c_void_p]
     lib.oracle_gradient.argtypes = [C.c_void_p, P(C.c_double), C.c_size_t]
+    lib.oracle_paper_objective.argtypes = [C.c_void_p, P(C.c_double)]
+    lib.oracle_paper_gradient.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double), C.c_size_t]
     lib.oracle_reset.argtypes = [C.c_void_p]
     lib.oracle_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
     lib.oracle_get_field.argtypes = [C.c_void_p, C.c_int, P(C.c_double), C.c_size_t]
@@ -171,6 +173,19 @@ class Oracle:
         g = np.zeros(self.dshape, dtype=np.float64)
         self._check(self.lib.oracle_gradient(self.h, _dptr(g), g.size), "gradient")
         return g
+
+    def paper_objective(self):
+        """Time-domain objective of Eq. (Objective_analyitically_enhancement) (paper mode)."""
+        F = C.c_double()
+        self._check(self.lib.oracle_paper_objective(self.h, C.byref(F)), "paper_objective")
+        return F.value
+
+    def paper_gradient(self, align=0):
+        """(F_td, gradient of Eq. (Gradient_FDTD) per design voxel); align: see fdtd_oracle.h."""
+        F = C.c_double()
+        g = np.zeros(self.dshape, dtype=np.float64)
+        self._check(self.lib.oracle_paper_gradient(self.h, int(align), C.byref(F), _dptr(g), g.size), "paper_gradient")
+        return F.value, g
 
     def reset(self):
         self._check(self.lib.oracle_reset(self.h), "reset")

@@ -740,6 +740,160 @@ int oracle_adjoint(oracle_ctx* c)
 }
 
 /* ---------------------------------------------------------------------------------------------
+ * Paper mode (see the header): the time-domain energy objective and Eq. (Gradient_FDTD) with
+ * stored histories.  Histories cover every owned sample of the design box, n = 0..M.
+ * ------------------------------------------------------------------------------------------- */
+static double gap_energy(const oracle_ctx* c)
+{
+    const int* gb = c->g.gap_box;
+    double s = 0.0;
+    for (int comp = 0; comp < 3; ++comp)
+        for (int k = gb[4]; k < gb[5]; ++k)
+            for (int j = gb[2]; j < gb[3]; ++j)
+                for (int i = gb[0]; i < gb[1]; ++i) {
+                    double e = c->E[comp][lin(c, i, j, k)];
+                    s += e * e;
+                }
+    return s;
+}
+
+static void record_E(const oracle_ctx* c, double* hist, int n, int M)
+{
+    const int* b = c->g.design_box;
+    for (int comp = 0; comp < 3; ++comp)
+        for (int k = b[4]; k < b[5]; ++k)
+            for (int j = b[2]; j < b[3]; ++j)
+                for (int i = b[0]; i < b[1]; ++i) {
+                    size_t s = (size_t)comp * c->nd + design_index(c, i, j, k);
+                    hist[s * (size_t)(M + 1) + n] = c->E[comp][lin(c, i, j, k)];
+                }
+}
+
+/* Q histories: [comp][design voxel][pole][n] */
+static void record_Q(const oracle_ctx* c, cplx* qh[3], int n, int M)
+{
+    for (int comp = 0; comp < 3; ++comp)
+        for (size_t v = 0; v < c->nd; ++v)
+            for (int p = 0; p < c->P[comp]; ++p)
+                qh[comp][(v * (size_t)c->P[comp] + p) * (size_t)(M + 1) + n] = c->Q[comp][v * (size_t)c->P[comp] + p];
+}
+
+static int paper_forward(oracle_ctx* c, double* F_out, double* eh, cplx* qh[3])
+{
+    if (!c->have_mat) return fail(c, "materials not set");
+    if (c->nd && !c->have_rho) return fail(c, "density not set");
+    if (!c->ngap) return fail(c, "paper mode needs a gap");
+    const int M = c->g.n_steps;
+    oracle_reset(c);
+    if (c->g.src_kind == 1) {
+        c->inc_ready = 0;
+        build_incident(c);
+    }
+    if (eh) record_E(c, eh, 0, M);
+    if (qh[0] || qh[1] || qh[2]) record_Q(c, qh, 0, M);
+    double s = 0.0;
+    for (int n = 0; n < M; ++n) {
+        step_once(c, n, 1);
+        s += gap_energy(c);
+        if (eh) record_E(c, eh, n + 1, M);
+        if (qh[0] || qh[1] || qh[2]) record_Q(c, qh, n + 1, M);
+    }
+    const double dV = c->g.dx * c->g.dx * c->g.dx;
+    *F_out = 0.5 * EPS0 * dV * c->dt * s;
+    return 0;
+}
+
+int oracle_paper_objective(oracle_ctx* c, double* F_out)
+{
+    if (!c || !F_out) return 1;
+    cplx* none[3] = {NULL, NULL, NULL};
+    return paper_forward(c, F_out, NULL, none);
+}
+
+int oracle_paper_gradient(oracle_ctx* c, int align, double* F_out, double* grad, size_t n)
+{
+    if (!c || !grad) return 1;
+    if (n != c->nd) return fail(c, "gradient size %zu != %zu design voxels", n, c->nd);
+    const int M = c->g.n_steps;
+    const size_t ns = 3 * c->nd, L = (size_t)M + 1;
+    double* eh = (double*)zalloc(ns * L, sizeof(double));     /* forward E^n */
+    double* ah = (double*)zalloc(ns * L, sizeof(double));     /* adjoint Etilde^m */
+    cplx* qh[3];
+    for (int comp = 0; comp < 3; ++comp) qh[comp] = (cplx*)zalloc(c->nd * (size_t)(c->P[comp] ? c->P[comp] : 1) * L, sizeof(cplx));
+    double F = 0.0;
+    int rc = paper_forward(c, &F, eh, qh);
+    if (!rc) {
+        /* adjoint drive at every gap sample: the time-reversed functional derivative eps0 E */
+        const int* gb = c->g.gap_box;
+        const int delay = align & 1;
+        for (int comp = 0; comp < 3; ++comp)
+            for (int k = gb[4]; k < gb[5]; ++k)
+                for (int j = gb[2]; j < gb[3]; ++j)
+                    for (int i = gb[0]; i < gb[1]; ++i) {
+                        size_t gs = (size_t)comp * c->ngap + gap_index(c, i, j, k);
+                        size_t ds = (size_t)comp * c->nd + design_index(c, i, j, k);
+                        for (int m = 0; m < M; ++m) {
+                            int nf = M - m - delay;
+                            c->adjw[gs * (size_t)M + m] = nf >= 0 ? EPS0 * eh[ds * L + nf] : 0.0;
+                        }
+                    }
+        oracle_reset(c);
+        record_E(c, ah, 0, M);
+        for (int m = 0; m < M; ++m) {
+            step_once(c, m, 2);
+            record_E(c, ah, m + 1, M);
+        }
+        /* Eq. (Gradient_FDTD) per owned sample, summed over the voxel's three samples, times dx^3 */
+        const int shift = (align >> 1) & 1;   /* Etilde^{m+1/2} -> solver level m + shift */
+        const double dV = c->g.dx * c->g.dx * c->g.dx;
+        const int* b = c->g.design_box;
+        for (int k = b[4]; k < b[5]; ++k)
+            for (int j = b[2]; j < b[3]; ++j)
+                for (int i = b[0]; i < b[1]; ++i) {
+                    size_t v = design_index(c, i, j, k);
+                    if (voxel_class(c, i, j, k) != 1) {
+                        grad[v] = 0.0;
+                        continue;
+                    }
+                    double rho = c->rho[v], g = 0.0;
+                    for (int comp = 0; comp < 3; ++comp) {
+                        const double* E = eh + ((size_t)comp * c->nd + v) * L;
+                        const double* A = ah + ((size_t)comp * c->nd + v) * L;
+                        double deps = c->m2.eps_inf[comp] - c->m1.eps_inf[comp];
+                        double dsig = c->m2.sigma[comp] - c->m1.sigma[comp] + (1.0 - 2.0 * rho) * c->gamma;
+                        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+                        for (int m = 1; m <= M; ++m) {
+                            int lp = m + shift, lm = m - 1 + shift;
+                            double ap = lp <= M ? A[lp] : 0.0, am = lm >= 0 && lm <= M ? A[lm] : 0.0;
+                            double e = E[M - m];
+                            t1 += e * (ap - am);
+                            t2 += e * 0.5 * (ap + am);
+                            double dq = 0.0;
+                            for (int p = 0; p < c->P[comp]; ++p) {
+                                const cplx* q = qh[comp] + (v * (size_t)c->P[comp] + p) * L;
+                                double dk = p < c->P1[comp] ? -1.0 : 1.0;   /* d kappa_1/d rho = -1, d kappa_2/d rho = +1 */
+                                dq += dk * creal(q[M - m] - q[M - m + 1]);
+                            }
+                            /* the printed average of the two adjoint half-levels, or (align bit 2) the one
+                             * level the eps_inf term's summation by parts pairs with this Q difference */
+                            t3 += 2.0 * dq * ((align & 4) ? am : 0.5 * (ap + am));
+                        }
+                        g += -EPS0 * deps * t1 - dsig * t2 * c->dt + t3;
+                    }
+                    grad[v] = g * dV;
+                }
+    }
+    for (int comp = 0; comp < 3; ++comp) free(qh[comp]);
+    free(eh);
+    free(ah);
+    if (rc) return rc;
+    if (F_out) *F_out = F;
+    c->have_fwd = 0;     /* the DFT-mode forward state is not valid after paper mode */
+    c->have_adj = 0;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------------
  * Gradient.  With z = e^{j w dt}, the z-transform of the E update of a sample gives its discrete
  * admittance  Y(z) = (1/dt)[eps0 eps_inf (z-1) + sigma dt (z+1)/2 + sum_i kappa_i sum_p (z-1)(h_p + hb_p)],
  * h_p = beta_p (z+1)/(z-alpha_p), hb_p the same with conj(alpha_p), conj(beta_p) (the conjugate

@@ -75,6 +75,20 @@ int oracle_forward(oracle_ctx* c, double* F_out, double* gap_dft_out);
 int oracle_adjoint(oracle_ctx* c);
 int oracle_gradient(oracle_ctx* c, double* grad, size_t n);
 
+/* Paper mode (tiny grids): the time-domain objective of Eq. (Objective_analyitically_enhancement),
+ *   F_td = (eps0/2) dx^3 dt sum_{n=1..M} sum_{gap samples} (E^n)^2   (air in the gap),
+ * from a forward run.  oracle_paper_gradient also runs the adjoint system of SI Eq. (AdjointSystem)
+ * (the same solver, driven at the gap samples by the time-reversed functional derivative eps0 E)
+ * and evaluates the paper's discrete gradient Eq. (Gradient_FDTD) from the stored forward E and Q
+ * and adjoint E histories, times dx^3, per design voxel (the three owned samples share rho; gap
+ * voxels 0).  The paper leaves the half-step alignment open: align bit 0 delays the adjoint drive
+ * by one step (E^{M-m-1} instead of E^{M-m} at adjoint step m), bit 1 maps the adjoint levels
+ * Etilde^{m +- 1/2} to the solver's Etilde^{m+1}, Etilde^{m} (else Etilde^{m}, Etilde^{m-1}); bit 2
+ * pairs the pole term's Q difference with Etilde^{m-1/2} alone instead of the printed average of
+ * Etilde^{m+1/2} and Etilde^{m-1/2}. */
+int oracle_paper_objective(oracle_ctx* c, double* F_out);
+int oracle_paper_gradient(oracle_ctx* c, int align, double* F_out, double* grad, size_t n);
+
 /* Test hooks. */
 int oracle_reset(oracle_ctx* c);
 int oracle_step(oracle_ctx* c, int n_first, int n_count, int source_mode); /* 0 none 1 fwd 2 adj */
