@@ -39,7 +39,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "f3_Au", "f3_Al", "f3_Si", "f3_TiO2"])
     ap.add_argument("--time-steps", type=int, default=0, help="override the workload's time steps")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-steps", type=int, default=16,
@@ -162,12 +162,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
+def set_steps(d, M):
+    """Set a description's time steps; a sampled source waveform is cut to the new window (its
+    first 2 M + 1 half-step samples are the same function of time)."""
+    if d.get("src_wave") is not None:
+        if 2 * M + 1 > len(d["src_wave"]):
+            raise ValueError("more time steps than the source waveform covers")
+        d["src_wave"] = d["src_wave"][:2 * M + 1]
+    d["n_steps"] = M
+
+
 def workload_and_config(args):
     import synth
-    w = synth.workload(args.workload)
+    if args.workload.startswith("f3_"):
+        w = synth.paper_workload(args.workload[3:])
+    else:
+        w = synth.workload(args.workload)
     d = w["desc"]
     if args.time_steps:
-        d["n_steps"] = args.time_steps
+        set_steps(d, args.time_steps)
     ncell = d["nx"] * d["ny"] * d["nz"]
     dshape = synth.box_shape(d["design_box"])
     poles = [len(w["m1"]["poles"][0]) + len(w["m2"]["poles"][0])]
@@ -181,7 +194,12 @@ def workload_and_config(args):
             "c3": "config 3: 512x512x384 grid, 16-cell CPML, 6000 steps, 256x256x192 design, 2-pair "
                   "Lorentz dielectric | 4-pair metal, FP32",
             "c4": "config 4: 64^3 grid, 2000 steps, 32^3 design, 2-pair metal, rho in [0.2,0.8]",
-        }[args.workload],
+        }.get(args.workload) or (
+            f"the paper's setup with {args.workload[3:]}: design 25x100x100 / gap 25x6x6 cells (the paper's "
+            "100x25x100 / 6x25x6 with x and y exchanged), z-polarised plane wave along x carrying the "
+            "truncated sinc x Hanning pulse at 576.5 THz, 20-cell CPML, 15 air cells of padding, "
+            f"dx={'2' if args.workload[3:] in ('Al', 'Au') else '5'} nm, dt=dx/(2c0), air | Table-1 "
+            f"{args.workload[3:]}, 8 objective frequencies over 350-1000 nm, FP32 fields + FP64 DFT"),
         "grid": [d["nx"], d["ny"], d["nz"]], "time_steps": d["n_steps"], "design": list(dshape[::-1]),
         "pole_pairs_total": poles[0], "n_freq": len(d["freqs_hz"]), "precision": d["precision"],
         "dft_accumulators": "f64", "parallelism": f"replicas x{args.gpus}",
@@ -232,7 +250,7 @@ def cpu_baseline(args, w_full):
 
     import oracle
     w = copy.deepcopy(w_full)
-    w["desc"]["n_steps"] = args.cpu_sample_steps
+    set_steps(w["desc"], args.cpu_sample_steps)
     d = w["desc"]
     ncell = d["nx"] * d["ny"] * d["nz"]
     t0 = time.perf_counter()
@@ -285,7 +303,7 @@ def precision_study(args):
     import synth
     w = synth.workload("c3")
     if args.time_steps:
-        w["desc"]["n_steps"] = args.time_steps
+        set_steps(w["desc"], args.time_steps)
     out = {}
     res = {}
     for prec in (64, 32):
@@ -330,7 +348,7 @@ def run_reference(args):
 
     import oracle
     ws = copy.deepcopy(w)
-    ws["desc"]["n_steps"] = args.cpu_sample_steps
+    set_steps(ws["desc"], args.cpu_sample_steps)
     o = oracle.problem(ws)
     times = []
     for s in range(args.warmup + args.steps):

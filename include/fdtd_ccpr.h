@@ -64,8 +64,11 @@ typedef enum {
  *    first total-field plane x = src_pos[0] dx, incident field src_amp p(t) from a matched 1-D line.
  *    p(t) = exp(-(t-t0)^2/(2 tau^2)) sin(2 pi f0 (t-t0)), tau = sqrt(2 ln 2)/(pi src_fwhm_hz),
  *    t0 = src_t0 or 4 tau if src_t0 <= 0.
+ *  src_wave: optional source waveform p(s dt/2), s = 0 .. 2 n_steps (2 n_steps + 1 doubles, copied
+ *    during fdtd_create_grid), replacing the Gaussian pulse for either source kind (e.g. the
+ *    paper's truncated sinc x Hanning window x carrier of Sec. "Optimization setup"); NULL: p above.
  *  adj_tau: envelope of the 2F adjoint basis pulses g(t){cos,sin}(w_f (t - 4 adj_tau));
- *    <= 0 selects the source's tau. */
+ *    <= 0 selects the source's tau (then src_fwhm_hz > 0 is required even with src_wave). */
 typedef struct {
     int nx, ny, nz;
     double dx;
@@ -84,6 +87,7 @@ typedef struct {
     int src_pos[3];
     double src_f0, src_fwhm_hz, src_t0, src_amp;
     double adj_tau;
+    const double* src_wave;
 } fdtd_grid_desc;
 
 /* One CCPR material (Eq. (CCPRModel)): per Cartesian component k, eps_inf[k], sigma[k] (S/m)

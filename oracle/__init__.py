@@ -26,7 +26,7 @@ class _Desc(C.Structure):
                 ("freq_weights", C.POINTER(C.c_double)),
                 ("src_kind", C.c_int), ("src_comp", C.c_int), ("src_pos", C.c_int * 3),
                 ("src_f0", C.c_double), ("src_fwhm_hz", C.c_double), ("src_t0", C.c_double),
-                ("src_amp", C.c_double), ("adj_tau", C.c_double)]
+                ("src_amp", C.c_double), ("adj_tau", C.c_double), ("src_wave", C.POINTER(C.c_double))]
 
 
 class _Mat(C.Structure):
@@ -121,6 +121,11 @@ class Oracle:
         d.n_freq = len(self._freqs)
         d.freqs_hz = _dptr(self._freqs)
         d.freq_weights = _dptr(self._w)
+        if desc.get("src_wave") is not None:
+            self._wave = np.ascontiguousarray(desc["src_wave"], dtype=np.float64)
+            if self._wave.size != 2 * int(desc["n_steps"]) + 1:
+                raise ValueError("src_wave needs 2 n_steps + 1 samples (t = s dt / 2)")
+            d.src_wave = _dptr(self._wave)
         self._d = d
         h = C.c_void_p()
         if self.lib.oracle_create(C.byref(d), C.byref(h)) != 0:

@@ -66,6 +66,7 @@ struct oracle_ctx {
     double* einc;             /* E_inc^n at the first total-field plane */
     double* hinc;             /* H_inc^{n+1/2} half a cell before it */
     double* adjw;             /* adjoint drive [3*ngap][M] */
+    double* wave;             /* copy of src_wave, or NULL */
     int inc_ready;            /* einc/hinc built for the current background */
     double F;
     char err[512];
@@ -150,8 +151,13 @@ static double stretched(double dF, double kap, double b, double cc, double* psi)
 static double src_tau(const oracle_grid_desc* g) { return sqrt(2.0 * log(2.0)) / (M_PI * g->src_fwhm_hz); }
 static double src_t0(const oracle_grid_desc* g) { return g->src_t0 > 0.0 ? g->src_t0 : 4.0 * src_tau(g); }
 
-static double pulse(const oracle_grid_desc* g, double t)
+/* Source waveform p(t) (t a multiple of dt/2): the caller's samples if given, else the Gaussian pulse. */
+static double pulse_w(const oracle_grid_desc* g, double dt, double t)
 {
+    if (g->src_wave) {
+        long s = lround(2.0 * t / dt);
+        return (s >= 0 && s <= 2L * g->n_steps) ? g->src_wave[s] : 0.0;
+    }
     double tau = src_tau(g), t0 = src_t0(g);
     double x = t - t0;
     return exp(-x * x / (2.0 * tau * tau)) * sin(2.0 * M_PI * g->src_f0 * x);
@@ -178,7 +184,7 @@ void oracle_destroy(oracle_ctx* c)
         free(c->alpha[a]); free(c->beta[a]); free(c->Q[a]);
     }
     free_mat(&c->bg); free_mat(&c->m1); free_mat(&c->m2);
-    free(c->freqs); free(c->fw); free(c->rho);
+    free(c->freqs); free(c->fw); free(c->rho); free(c->wave);
     free(c->dft[0]); free(c->dft[1]);
     free(c->src); free(c->einc); free(c->hinc); free(c->adjw);
     free(c);
@@ -232,6 +238,11 @@ int oracle_create(const oracle_grid_desc* d, oracle_ctx** out)
     }
     c->g.freqs_hz = c->freqs;
     c->g.freq_weights = c->fw;
+    if (d->src_wave) {
+        c->wave = (double*)zalloc(2 * (size_t)d->n_steps + 1, sizeof(double));
+        memcpy(c->wave, d->src_wave, (2 * (size_t)d->n_steps + 1) * sizeof(double));
+    }
+    c->g.src_wave = c->wave;
     for (int a = 0; a < 3; ++a) {
         c->E[a] = (double*)zalloc(c->ncell, sizeof(double));
         c->H[a] = (double*)zalloc(c->ncell, sizeof(double));
@@ -264,7 +275,7 @@ int oracle_create(const oracle_grid_desc* d, oracle_ctx** out)
             if (d->src_pos[a] < 0 || d->src_pos[a] >= c->n[a]) { fail(c, "dipole outside grid"); goto bad; }
         if (d->src_comp < 0 || d->src_comp > 2) { fail(c, "bad dipole component"); goto bad; }
         /* soft source of amplitude A (V/m per step in vacuum): drive = A (eps0/dt) p(t) */
-        for (int n = 0; n < M; ++n) c->src[n] = d->src_amp * (EPS0 / c->dt) * pulse(d, (n + 0.5) * c->dt);
+        for (int n = 0; n < M; ++n) c->src[n] = d->src_amp * (EPS0 / c->dt) * pulse_w(&c->g, c->dt, (n + 0.5) * c->dt);
     } else if (d->src_kind == 1) {
         int i0 = d->src_pos[0];
         if (i0 < d->cpml[0] + 1 || i0 >= c->n[0] - d->cpml[1]) { fail(c, "TF/SF plane inside the CPML"); goto bad; }
@@ -552,7 +563,7 @@ static void build_incident(oracle_ctx* c)
     const double dt = c->dt, dx = g->dx;
     double eps = c->bg.eps_inf[2], sig = c->bg.sigma[2];
     double D = EPS0 * eps / dt + sig / 2.0, N = EPS0 * eps / dt - sig / 2.0;
-    e1[0] = g->src_amp * pulse(g, 0.0);
+    e1[0] = g->src_amp * pulse_w(g, dt, 0.0);
     for (int n = 0; n < M; ++n) {
         c->einc[n] = e1[off];
         for (int m = 0; m < L; ++m) {
@@ -561,7 +572,7 @@ static void build_incident(oracle_ctx* c)
         }
         c->hinc[n] = h1[off - 1];
         for (int m = 1; m < L; ++m) e1[m] = (N * e1[m] + (h1[m] - h1[m - 1]) / dx) / D;
-        e1[0] = g->src_amp * pulse(g, (n + 1) * dt);
+        e1[0] = g->src_amp * pulse_w(g, dt, (n + 1) * dt);
     }
     free(e1);
     free(h1);

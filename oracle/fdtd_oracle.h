@@ -50,6 +50,8 @@ typedef struct {
     int src_pos[3];              /* dipole voxel; for TF/SF src_pos[0] is the first total-field x index */
     double src_f0, src_fwhm_hz, src_t0, src_amp;
     double adj_tau;              /* envelope of the adjoint basis pulses (0: the source's) */
+    const double* src_wave;      /* optional p(s dt/2), s = 0..2 n_steps, replacing the Gaussian pulse
+                                    (copied at create) */
 } oracle_grid_desc;
 
 typedef struct {

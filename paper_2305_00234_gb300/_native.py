@@ -36,7 +36,7 @@ class GridDesc(C.Structure):
                 ("freq_weights", C.POINTER(C.c_double)),
                 ("src_kind", C.c_int), ("src_comp", C.c_int), ("src_pos", C.c_int * 3),
                 ("src_f0", C.c_double), ("src_fwhm_hz", C.c_double), ("src_t0", C.c_double),
-                ("src_amp", C.c_double), ("adj_tau", C.c_double)]
+                ("src_amp", C.c_double), ("adj_tau", C.c_double), ("src_wave", C.POINTER(C.c_double))]
 
 
 class Material(C.Structure):
@@ -126,6 +126,12 @@ def make_desc(desc, keep):
     g.n_freq = f.size
     g.freqs_hz = _dptr(f)
     g.freq_weights = _dptr(w)
+    if desc.get("src_wave") is not None:
+        wv = np.ascontiguousarray(desc["src_wave"], dtype=np.float64)
+        if wv.size != 2 * int(desc["n_steps"]) + 1:
+            raise ValueError("src_wave needs 2 n_steps + 1 samples (t = s dt / 2)")
+        keep.append(wv)
+        g.src_wave = _dptr(wv)
     return g
 
 

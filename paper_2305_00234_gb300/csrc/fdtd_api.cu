@@ -125,8 +125,13 @@ void pml_point(const fdtd_grid_desc& d, double dt, int lo, int hi, int n, double
 
 double src_tau(const fdtd_grid_desc& d) { return std::sqrt(2.0 * std::log(2.0)) / (kPi * d.src_fwhm_hz); }
 
-double src_pulse(const fdtd_grid_desc& d, double t)
+// Source waveform at t (a multiple of dt/2): the caller's samples if given, else the Gaussian pulse.
+double src_pulse(const fdtd_grid_desc& d, double dt, double t)
 {
+    if (d.src_wave) {
+        const long s = std::lround(2.0 * t / dt);
+        return (s >= 0 && s <= 2L * d.n_steps) ? d.src_wave[s] : 0.0;
+    }
     const double tau = src_tau(d);
     const double t0 = d.src_t0 > 0.0 ? d.src_t0 : 4.0 * tau;
     const double x = t - t0;
@@ -177,7 +182,12 @@ void validate(const fdtd_grid_desc& d)
     } else {
         arg_error("src_kind must be 0 (dipole) or 1 (TF/SF plane)");
     }
-    if (!(d.src_fwhm_hz > 0.0) || !(d.src_f0 >= 0.0) || !std::isfinite(d.src_amp)) arg_error("bad source parameters");
+    if (!std::isfinite(d.src_amp)) arg_error("bad source amplitude");
+    if (!d.src_wave && (!(d.src_fwhm_hz > 0.0) || !(d.src_f0 >= 0.0))) arg_error("bad source parameters");
+    if (!(d.adj_tau > 0.0) && !(d.src_fwhm_hz > 0.0)) arg_error("adjoint pulses need adj_tau > 0 or src_fwhm_hz > 0");
+    if (d.src_wave)
+        for (long s = 0; s <= 2L * d.n_steps; ++s)
+            if (!std::isfinite(d.src_wave[s])) arg_error("non-finite source waveform sample");
 }
 
 size_t footprint(const fdtd_grid_desc& d, const int ptot[3])
@@ -258,7 +268,7 @@ struct SolverBase {
 
 struct fdtd_ctx {
     fdtd_grid_desc d{};
-    std::vector<double> freqs, weights;
+    std::vector<double> freqs, weights, wave;
     cudaStream_t user = nullptr, work = nullptr;
     cudaStream_t side = nullptr;                       // second branch of the captured step graph
     cudaEvent_t fence = nullptr, fork = nullptr, join = nullptr;
@@ -496,7 +506,7 @@ struct Solver : SolverBase {
         const fdtd_grid_desc& d = c->d;
         if (d.src_kind == 0) {
             std::vector<T> w(d.n_steps), r(3, T(0));
-            for (int s = 0; s < d.n_steps; ++s) w[s] = (T)src_pulse(d, (s + 0.5) * c->dt);
+            for (int s = 0; s < d.n_steps; ++s) w[s] = (T)src_pulse(d, c->dt, (s + 0.5) * c->dt);
             r[d.src_comp] = (T)(d.src_amp * kEps0 / c->dt);
             CK(cudaMemcpyAsync(src_wave[0], w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, c->work));
             CK(cudaMemcpyAsync(src_r[0], r.data(), 3 * sizeof(T), cudaMemcpyHostToDevice, c->work));
@@ -527,14 +537,14 @@ struct Solver : SolverBase {
         const double Dp = kEps0 * bg.eps[2] / dt + 0.5 * bg.sig[2];
         const double Dm = kEps0 * bg.eps[2] / dt - 0.5 * bg.sig[2];
         const double chx = dt / (kMu0 * dx);
-        e[0] = d.src_amp * src_pulse(d, 0.0);
+        e[0] = d.src_amp * src_pulse(d, c->dt, 0.0);
         for (int s = 0; s < M; ++s) {
             ei[s] = (T)e[off];
             for (int m = 0; m + 1 < L; ++m) h[m] += chx * (e[m + 1] - e[m]);
             h[L - 1] += chx * (0.0 - e[L - 1]);
             hi[s] = (T)h[off - 1];
             for (int m = 1; m < L; ++m) e[m] = (Dm * e[m] + (h[m] - h[m - 1]) / dx) / Dp;
-            e[0] = d.src_amp * src_pulse(d, (s + 1) * dt);
+            e[0] = d.src_amp * src_pulse(d, c->dt, (s + 1) * dt);
         }
         CK(cudaMemcpyAsync(einc, ei.data(), M * sizeof(T), cudaMemcpyHostToDevice, c->work));
         CK(cudaMemcpyAsync(hinc, hi.data(), M * sizeof(T), cudaMemcpyHostToDevice, c->work));
@@ -1216,6 +1226,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd
         if (desc->freq_weights) c->weights.assign(desc->freq_weights, desc->freq_weights + desc->n_freq);
         c->d.freqs_hz = c->freqs.data();
         c->d.freq_weights = c->weights.data();
+        if (desc->src_wave) {
+            c->wave.assign(desc->src_wave, desc->src_wave + 2 * (size_t)desc->n_steps + 1);
+            c->d.src_wave = c->wave.data();
+        }
         CK(cudaGetDevice(&c->device));
         c->user = (cudaStream_t)cuda_stream;
         CK(cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking));

@@ -160,7 +160,49 @@ def base_desc(nx, ny, nz, *, dx=5e-9, courant=0.99 / math.sqrt(3.0), n_steps=100
             "design_box": design_box, "gap_box": gap_box,
             "freqs_hz": freqs, "freq_weights": w,
             "src_kind": src_kind, "src_comp": src_comp, "src_pos": list(src_pos),
-            "src_f0": f0, "src_fwhm_hz": fwhm, "src_t0": 0.0, "src_amp": src_amp, "adj_tau": 0.0}
+            "src_f0": f0, "src_fwhm_hz": fwhm, "src_t0": 0.0, "src_amp": src_amp, "adj_tau": 0.0,
+            "src_wave": None}
+
+
+def sinc_hann_wave(n_steps, dt, f_c=576.5e12, rel_bw=0.5, lobes=3):
+    """The paper's excitation (Sec. "Optimization setup", Fig. "Signal"): a sinc envelope truncated to
+    `lobes` zero crossings either side of its peak, times a Hanning window over the same span,
+    modulating a carrier f_c (576.5 THz, the centre of the 350-1000 nm window).  The sinc's spectrum
+    is a rectangle of full width rel_bw * f_c (~50% at half maximum).  Sampled at t = s dt / 2,
+    s = 0 .. 2 n_steps, the half-step grid the solvers read (src_wave)."""
+    B = rel_bw * f_c
+    half = lobes / B                      # sinc(B x) vanishes at x = k / B
+    x = np.arange(2 * n_steps + 1) * (dt / 2.0) - half
+    win = np.where(np.abs(x) <= half, 0.5 * (1.0 + np.cos(np.pi * x / half)), 0.0)
+    return np.sinc(B * x) * win * np.sin(2.0 * np.pi * f_c * x)
+
+
+def paper_workload(material="Au", seed=None, n_freq=8, n_steps=None, pad=15, cpml=20, design=(25, 100, 100),
+                   gap=(25, 6, 6), precision=32):
+    """The paper's own optimisation setup (Sec. "Optimization setup" and "Technical details"):
+    Omega_d 100 x 25 x 100 and Omega_g 6 x 25 x 6 Yee cells, z-polarised plane wave along y carrying
+    the truncated-sinc pulse, 20-cell CPML, dx = 2 nm (Al, Au) or 5 nm (Si, TiO2), dt = dx / (2 c0),
+    18000 (metals) or 10000 (dielectrics) steps, air | Table-1 material.  Here x and y are exchanged
+    (the plane wave travels along +x through the TF/SF plane; every Table-1 material has equal x and y
+    components), `pad` air cells separate the design box from the CPML (the paper gives none), and
+    the time-domain energy objective is represented by n_freq frequencies evenly spaced over
+    350-1000 nm with equal weights (a uniform quadrature of its spectrum by Parseval)."""
+    idx = {"Al": 11, "Au": 12, "Si": 13, "TiO2": 14}[material]
+    seed = SEED_BASE + idx if seed is None else seed
+    metal = material in ("Al", "Au")
+    dx = 2e-9 if metal else 5e-9
+    M = n_steps if n_steps is not None else (18000 if metal else 10000)
+    nx = 2 * (cpml + pad) + design[0]
+    nx += (-nx) % 4                       # x rows of a multiple of 16 bytes (fused interior kernel)
+    ny = 2 * (cpml + pad) + design[1]
+    nz = 2 * (cpml + pad) + design[2]
+    f = np.linspace(C0 / 1000e-9, C0 / 350e-9, n_freq)
+    d = base_desc(nx, ny, nz, dx=dx, courant=0.5, n_steps=M, cpml=cpml, precision=precision, design=design,
+                  gap=gap, lambdas_nm=tuple(C0 / f * 1e9), src_kind=1, src_pos=(cpml + 2, 0, 0))
+    dt = 0.5 * dx / C0
+    d["src_wave"] = sinc_hann_wave(M, dt)
+    rho = smooth_rho(box_shape(d["design_box"]), seed + 1000, 3.0)
+    return dict(desc=d, bg=vacuum(), m1=vacuum(), m2=table_material(material), gamma=0.0, rho=rho, seed=seed)
 
 
 def box_shape(box):

@@ -356,6 +356,42 @@ def test_tfsf_no_leakage():
 
 
 # ----------------------------------------------------------------------------------------------
+# A source waveform passed as samples (src_wave, p(s dt/2)) drives the same run as the built-in
+# pulse it samples, for both source kinds; the paper's truncated-sinc pulse has the spectrum the
+# setup section describes (carrier 576.5 THz, ~50% band at half maximum inside 350-1000 nm).
+# ----------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [0, 1])
+def test_src_wave_samples_equal_builtin_pulse(kind):
+    M = 300
+    d = base_desc(24, 20, 20, n_steps=M, cpml=4, precision=64, src_kind=kind, src_pos=(7, 10, 10))
+    dt = d["courant"] * d["dx"] / C0
+    tau = math.sqrt(2.0 * math.log(2.0)) / (math.pi * d["src_fwhm_hz"])
+    t = np.arange(2 * M + 1) * dt / 2.0 - 4.0 * tau
+    d2 = dict(d, src_wave=np.exp(-t * t / (2.0 * tau * tau)) * np.sin(2.0 * math.pi * d["src_f0"] * t))
+    fields = []
+    for dd in (d, d2):
+        o = _oracle(dd)
+        o.step(0, M, 1)
+        fields.append([o.get_field(c) for c in range(6)])
+        o.close()
+    scale = max(np.max(np.abs(a)) for a in fields[0])
+    assert scale > 0
+    for a, b in zip(*fields):
+        assert np.max(np.abs(a - b)) <= 1e-12 * scale
+
+
+def test_paper_pulse_spectrum():
+    dt = 0.5 * 2e-9 / C0
+    wv = synth.sinc_hann_wave(18000, dt)[::2]
+    sp = np.abs(np.fft.rfft(wv, 1 << 17))
+    fr = np.fft.rfftfreq(1 << 17, dt)
+    band = fr[sp >= sp.max() / 2]
+    assert abs(0.5 * (band.min() + band.max()) - 576.5e12) < 0.01 * 576.5e12
+    assert 0.45 < (band.max() - band.min()) / 576.5e12 < 0.55
+    assert band.min() > C0 / 1000e-9 and band.max() < C0 / 350e-9
+
+
+# ----------------------------------------------------------------------------------------------
 # Normal-incidence reflection from a dispersive half-space (Table 1 gold): the measured
 # reflection equals the exact discrete interface formula, and the continuous Fresnel coefficient
 # (1-n)/(1+n) with n = sqrt(eps_CCPR) to the grid's discretisation error.

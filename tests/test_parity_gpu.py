@@ -118,6 +118,20 @@ def test_step_paths(gpu, prec, nx, fused, src):
     compare(g, run_oracle(w), prec)
 
 
+@pytest.mark.parametrize("material", ["Si", "Au"])
+def test_paper_workload_reduced(gpu, material):
+    """The paper's own setup (z-polarised plane wave carrying the truncated sinc x Hanning pulse,
+    Table-1 material in air, dt = dx/(2 c0), design box thin along the propagation axis, gap spanning
+    it) on a reduced grid with an interior box: design 24 x 32 x 32, gap 24 x 4 x 4, 8-cell CPML,
+    2400 steps, 4 objective frequencies over 350-1000 nm."""
+    w = synth.paper_workload(material, design=(24, 32, 32), gap=(24, 4, 4), pad=10, cpml=8, n_steps=2400,
+                             n_freq=4)
+    w["desc"]["adj_tau"] = 1.0e-15
+    g = run_gpu(gpu, w)
+    assert g["p"].timings()["fused_step"] == 1
+    compare(g, run_oracle(w), 32)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_config1_full(gpu, prec):
     """Config 1 at its full size: 32^3 FP64, 1000 steps, dipole, 2-pair metal, 16^3 design."""
