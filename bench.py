@@ -162,6 +162,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
+def cell_update_model(w, gcells, peak):
+    """HBM fraction of the whole run under the per-cell-update byte count of the method (FP32 state
+    words read once and written once per step, separate H and E passes): every cell 72 B (E, H r/w and
+    the other field read once per half-step); per design voxel 4 (rho) + 48 P_tot (pole currents r/w)
+    + 96 F (FP64 DFT accumulators r/w); per CPML slab cell and attenuated axis 32 B (two psi_E and two
+    psi_H r/w).  fraction = Gcell-updates/s x bytes per cell-update / peak."""
+    import synth
+    d = w["desc"]
+    ts = 4.0 if d["precision"] == 32 else 8.0
+    n = (d["nx"], d["ny"], d["nz"])
+    ncell = float(n[0] * n[1] * n[2])
+    bs = synth.box_shape(d["design_box"])
+    nd = float(bs[0] * bs[1] * bs[2]) if d["design_box"][1] > d["design_box"][0] else 0.0
+    p_tot = sum(len(w["m1"]["poles"][k]) + len(w["m2"]["poles"][k]) for k in range(3)) / 3.0
+    slab = sum((d["cpml"][2 * a] + d["cpml"][2 * a + 1]) / n[a] for a in range(3))
+    b = 18.0 * ts + nd / ncell * (ts + 12.0 * p_tot * ts + 96.0 * len(d["freqs_hz"])) + slab * 8.0 * ts
+    return {"bytes_per_cell_update": b, "achieved_gbs": gcells * b, "frac": gcells * b / peak,
+            "note": "per-cell-update byte model of the method (separate H and E passes); step_bytes_frac "
+                    "counts the bytes of this build's kernels (fused interior: 48 B per cell)"}
+
+
 def set_steps(d, M):
     """Set a description's time steps; a sampled source waveform is cut to the new window (its
     first 2 M + 1 half-step samples are the same function of time)."""
@@ -472,7 +493,8 @@ def run_ours(args):
             "avg_launch_ms": kd["avg_launch_ms"], "kernels": kern,
             "step_bytes_frac": sum(v["algorithmic_bytes_per_launch"] * v["launches"] for v in kern.values())
             / (elapsed_ms / 1e3) / 1e9 / peak,
-            "dft_steps_per_launch": tim["dft_steps_per_launch"]}
+            "dft_steps_per_launch": tim["dft_steps_per_launch"],
+            "cell_update_model": cell_update_model(w, value, peak)}
     launches = int(tim["launches"])
     # ---- end to end through the public API with host buffers ----
     e2e = None
