@@ -128,6 +128,28 @@ typedef struct {
  * by fdtd_footprint_bytes).  Errors: FDTD_ERR_ARG (invalid desc), FDTD_ERR_OOM, FDTD_ERR_CUDA. */
 fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd_handle* out);
 
+/* Paper mode: the paper's own objective and gradient, for comparison with the frequency-domain
+ * ones above.  fdtd_paper_forward runs the forward system and returns the time-domain energy
+ * objective of Eq. (Objective_analyitically_enhancement) over the gap,
+ *   F = (eps0/2) dx^3 dt sum_{n=1..M} sum_{gap samples} (E^n)^2,
+ * storing the full solver state every checkpoint_steps steps (<= 0: about sqrt(M x state / per-step
+ * history), the memory-optimal interval) and the gap field at every step.  fdtd_paper_gradient then
+ * evaluates Eq. (Gradient_FDTD) per design voxel (times dx^3; the voxel's three samples share rho; gap
+ * voxels 0) by checkpoint-recompute: segment by segment from the last, the forward state is restored
+ * and recomputed with the design-box E and pole-current term recorded, and the adjoint system of SI
+ * Eq. (AdjointSystem) (the same solver on a second state set, driven at the gap samples by the
+ * time-reversed functional derivative eps0 E) advances over the mirrored steps.  Readings of the
+ * half-step alignment: the adjoint drive at adjoint step m is eps0 E^{M-m-1}, and the adjoint levels
+ * m, m-1 stand for the paper's m+1/2, m-1/2.  pole_pairing 0 multiplies the pole term's
+ * Re{Q^{M-m} - Q^{M-m+1}} by the printed average of those two levels, 1 by level m-1 alone.
+ * Extra device memory: a second state set, one state checkpoint per segment and three
+ * (checkpoint_steps + 1) x 3 x design-voxel history buffers.  grad: n = design voxels, dtype 0 float32
+ * / 1 float64, on_device as for fdtd_gradient.  Errors: FDTD_ERR_ARG (no design box or gap; sizes),
+ * FDTD_ERR_STATE (gradient before a paper forward, or after a density or material change),
+ * FDTD_ERR_OOM, FDTD_ERR_UNSTABLE, FDTD_ERR_CUDA. */
+fdtd_status fdtd_paper_forward(fdtd_handle h, int checkpoint_steps, double* F_out);
+fdtd_status fdtd_paper_gradient(fdtd_handle h, int pole_pairing, void* grad, size_t n, int dtype, int on_device);
+
 /* Device bytes a handle with this description and these pole counts would allocate
  * (p_total[k] = poles of m1 + m2 on component k).  For admission control; allocates nothing. */
 fdtd_status fdtd_footprint_bytes(const fdtd_grid_desc* desc, const int p_total[3], size_t* bytes);

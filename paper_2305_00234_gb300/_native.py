@@ -21,7 +21,8 @@ EXPORTS = ("fdtd_create_grid", "fdtd_footprint_bytes", "fdtd_set_materials", "fd
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gradient_norm", "fdtd_get_field",
            "fdtd_get_dft", "fdtd_get_index_map", "fdtd_set_profiling", "fdtd_get_timings",
            "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy",
-           "fdtd_gradient_static", "fdtd_filter_project", "fdtd_filter_project_grad")
+           "fdtd_gradient_static", "fdtd_filter_project", "fdtd_filter_project_grad", "fdtd_paper_forward",
+           "fdtd_paper_gradient")
 
 
 class GridDesc(C.Structure):
@@ -83,6 +84,8 @@ def load_library():
         "fdtd_adjoint": [vp],
         "fdtd_gradient": [vp, vp, sz, i, i],
         "fdtd_gradient_norm": [vp, P(d)],
+        "fdtd_paper_forward": [vp, i, P(d)],
+        "fdtd_paper_gradient": [vp, i, vp, sz, i, i],
         "fdtd_get_field": [vp, i, P(d), sz],
         "fdtd_get_dft": [vp, i, P(d), sz],
         "fdtd_get_index_map": [vp, i, P(C.c_int32), sz],
@@ -224,6 +227,18 @@ def fdtd_adjoint(h):
 def fdtd_gradient(h, out):
     p, n, dt, dev, keep = _buffer(out)
     _check(h, load_library().fdtd_gradient(h, C.c_void_p(p), n, dt, dev), "fdtd_gradient")
+    return out
+
+
+def fdtd_paper_forward(h, checkpoint_steps=0):
+    v = C.c_double()
+    _check(h, load_library().fdtd_paper_forward(h, int(checkpoint_steps), C.byref(v)), "fdtd_paper_forward")
+    return v.value
+
+
+def fdtd_paper_gradient(h, out, pole_pairing=0):
+    p, n, dt, dev, keep = _buffer(out)
+    _check(h, load_library().fdtd_paper_gradient(h, int(pole_pairing), C.c_void_p(p), n, dt, dev), "fdtd_paper_gradient")
     return out
 
 

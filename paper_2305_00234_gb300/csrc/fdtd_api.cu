@@ -264,6 +264,7 @@ cudaMemPool_t device_pool(int device)
 struct SolverBase {
     virtual ~SolverBase() = default;
     virtual void interior_box(int ib[6]) const = 0;
+    virtual bool has_interior() const = 0;
 };
 
 struct fdtd_ctx {
@@ -342,6 +343,7 @@ struct Solver : SolverBase {
 
     explicit Solver(fdtd_ctx* ctx) : c(ctx) {}
     void interior_box(int ib[6]) const override { std::copy(base.ib, base.ib + 6, ib); }
+    bool has_interior() const override { return fused; }
     ~Solver() override
     {
         for (auto& g : graph)
@@ -550,8 +552,15 @@ struct Solver : SolverBase {
         CK(cudaMemcpyAsync(hinc, hi.data(), M * sizeof(T), cudaMemcpyHostToDevice, c->work));
     }
 
+    Material mat_m1, mat_m2;        // the design materials (paper-mode gradient constants)
+    double mat_gamma = 0.0;
+
     void set_materials(const Material& bg, const Material& m1, const Material& m2, double gamma)
     {
+        mat_m1 = m1;
+        mat_m2 = m2;
+        mat_gamma = gamma;
+        pm_have_fwd = false;
         const double dt = c->dt;
         PoleTable<T> tab;
         std::memset(&tab, 0, sizeof tab);
@@ -697,19 +706,20 @@ struct Solver : SolverBase {
     // Background part of one step: H of the shell and the fused interior (both read only the old
     // buffers), then E of the shell (reads the new H of its neighbours).  concurrent: the shell H runs
     // on the side stream next to the interior kernel (graph capture); else all three in order.
-    cudaError_t launch_background(const KParams<T>& q, int parity, bool concurrent)
+    cudaError_t launch_background(const KParams<T>& q, int parity, bool concurrent, const StepMaps* mp = nullptr)
     {
+        if (!mp) mp = maps;
         cudaError_t e = cudaSuccess;
         if (concurrent && fused) {
             e = cudaEventRecord(c->fork, c->work);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
             if (e == cudaSuccess) e = fdtd::launch_shell<T>(q, shell, false, c->side);
-            if (e == cudaSuccess) e = fdtd::launch_step<T>(q, maps[parity & 1], c->work);
+            if (e == cudaSuccess) e = fdtd::launch_step<T>(q, mp[parity & 1], c->work);
             if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(c->work, c->join, 0);
         } else {
             e = fdtd::launch_shell<T>(q, shell, false, c->work);
-            if (e == cudaSuccess && fused) e = fdtd::launch_step<T>(q, maps[parity & 1], c->work);
+            if (e == cudaSuccess && fused) e = fdtd::launch_step<T>(q, mp[parity & 1], c->work);
         }
         return e == cudaSuccess ? fdtd::launch_shell<T>(q, shell, true, c->work) : e;
     }
@@ -725,6 +735,284 @@ struct Solver : SolverBase {
             for (int t = 0; t < 2; ++t) std::swap(q.psiH[cc][t], q.psiHn[cc][t]);
         }
         return q;
+    }
+
+    // ---- paper mode ----------------------------------------------------------------------------
+    // The time-domain energy objective of Eq. (Objective_analyitically_enhancement) and its gradient by
+    // Eq. (Gradient_FDTD), with checkpoint-recompute instead of the paper's full histories: the forward
+    // run stores its whole state every C steps; the gradient pass takes the segments last first,
+    // recomputes each one recording the design-box E and the pole term, advances the adjoint system (a
+    // second state set, driven by the time-reversed gap field) over the mirrored steps recording its
+    // design-box E, and accumulates the segment's terms per voxel.  Reading of the half-step alignment:
+    // the adjoint drive is eps0 E^{M-m-1} at adjoint step m, and the adjoint levels m, m-1 stand for the
+    // paper's m+1/2, m-1/2.
+    struct StateSet {
+        T* fld[4] = {nullptr, nullptr, nullptr, nullptr};   // E, H, E', H' blocks (3 * cs each)
+        T* psiE[3][2] = {};
+        T* psiH[3][2] = {};
+        T* psiHn[3][2] = {};
+        cpx<T>* Q[3] = {};
+        int* ctl = nullptr;
+    };
+    bool pm_ready = false;
+    int pm_C = 0, pm_nseg = 0;
+    StateSet pm_b;                                   // adjoint state
+    StepMaps pm_maps[2]{};
+    KParams<T> pm_fwd{}, pm_rec{}, pm_adj{};         // forward pass, recompute pass, adjoint pass
+    unsigned char* pm_ckpt = nullptr;                // pm_nseg slabs of pm_ckpt_bytes
+    size_t pm_ckpt_bytes = 0;
+    T *pm_he = nullptr, *pm_ha = nullptr, *pm_hq = nullptr, *pm_gh = nullptr, *pm_drive = nullptr;
+    double *pm_td = nullptr, *pm_gsum = nullptr;
+    bool pm_have_fwd = false;
+
+    size_t psi_elems(int cc, int t) const
+    {
+        const int n[3] = {c->d.nx, c->d.ny, c->d.nz};
+        const int a = (cc + 1 + t) % 3;
+        return (size_t)(c->ncell / n[a]) * base.W[a];
+    }
+
+    // The state words of a step-parity view: E^n, H^{n-1/2}, psi_E, psi_H^{n-1/2}, Q.
+    std::vector<std::pair<void*, size_t>> state_regions(const KParams<T>& q) const
+    {
+        std::vector<std::pair<void*, size_t>> r;
+        r.push_back({q.E[0], 3 * cs * sizeof(T)});
+        r.push_back({q.H[0], 3 * cs * sizeof(T)});
+        for (int cc = 0; cc < 3; ++cc)
+            for (int t = 0; t < 2; ++t) {
+                const size_t m = psi_elems(cc, t);
+                if (m) {
+                    r.push_back({q.psiE[cc][t], m * sizeof(T)});
+                    r.push_back({q.psiH[cc][t], m * sizeof(T)});
+                }
+            }
+        for (int cc = 0; cc < 3; ++cc)
+            if (ptot[cc] && c->nd) r.push_back({q.Q[cc], c->nd * ptot[cc] * sizeof(cpx<T>)});
+        return r;
+    }
+
+    void copy_state(const KParams<T>& q, unsigned char* slab, bool save)
+    {
+        size_t off = 0;
+        for (auto& reg : state_regions(q)) {
+            if (save) CK(cudaMemcpyAsync(slab + off, reg.first, reg.second, cudaMemcpyDeviceToDevice, c->work));
+            else CK(cudaMemcpyAsync(reg.first, slab + off, reg.second, cudaMemcpyDeviceToDevice, c->work));
+            off += (reg.second + 255) / 256 * 256;
+        }
+    }
+
+    void pm_alloc(int C)
+    {
+        const fdtd_grid_desc& d = c->d;
+        const int M = d.n_steps;
+        if (c->nd == 0 || c->ngap == 0) arg_error("paper mode needs a design box with a gap");
+        if (!pm_b.fld[0]) {                      // adjoint state set, allocated once
+            for (int f = 0; f < 4; ++f) pm_b.fld[f] = talloc(3 * cs);
+            for (int cc = 0; cc < 3; ++cc)
+                for (int t = 0; t < 2; ++t) {
+                    const size_t m = psi_elems(cc, t);
+                    pm_b.psiE[cc][t] = talloc(m);
+                    pm_b.psiH[cc][t] = talloc(m);
+                    pm_b.psiHn[cc][t] = talloc(m);
+                }
+            for (int cc = 0; cc < 3; ++cc)
+                pm_b.Q[cc] = (cpx<T>*)c->alloc(c->nd * std::max(ptot[cc], 1) * sizeof(cpx<T>));
+            pm_b.ctl = (int*)c->alloc(4 * sizeof(int));
+            if (fused)
+                for (int par = 0; par < 2; ++par) {
+                    encode_map(&pm_maps[par].e, par ? pm_b.fld[2] : pm_b.fld[0], kSYE);
+                    encode_map(&pm_maps[par].h, par ? pm_b.fld[3] : pm_b.fld[1], kSYH);
+                }
+            const size_t ns = 3 * c->ngap;
+            pm_gh = talloc((size_t)M * ns);
+            pm_drive = talloc((size_t)M * ns);
+            pm_td = (double*)c->alloc(ns * sizeof(double));
+            pm_gsum = (double*)c->alloc(c->nd * sizeof(double));
+        }
+        pm_ckpt_bytes = 0;
+        for (auto& reg : state_regions(base)) pm_ckpt_bytes += (reg.second + 255) / 256 * 256;
+        const size_t step_hist = 3 * 3 * c->nd * sizeof(T);      // forward E, pole term, adjoint E per step
+        if (C <= 0) C = std::max(1, (int)std::lround(std::sqrt((double)M * pm_ckpt_bytes / step_hist)));
+        C = std::min(C, M);
+        if (pm_ready && C == pm_C) return;
+        pm_C = C;
+        pm_nseg = (M + C - 1) / C;
+        pm_ckpt = (unsigned char*)c->alloc((size_t)pm_nseg * pm_ckpt_bytes);
+        pm_he = talloc((size_t)(C + 1) * 3 * c->nd);
+        pm_ha = talloc((size_t)(C + 1) * 3 * c->nd);
+        pm_hq = talloc((size_t)C * 3 * c->nd);
+        pm_ready = true;
+    }
+
+    // Step parameters of the three passes, from the current materials and sources.
+    void pm_params()
+    {
+        const int C = pm_C;
+        // forward pass: the objective's gap energy and the gap field history (snapshots to scratch)
+        pm_fwd = pf;
+        pm_fwd.td_acc = pm_td;
+        pm_fwd.gap_hist = pm_gh;
+        pm_fwd.nsamp = (int)(3 * c->ngap);
+        pm_fwd.snap = pm_he;
+        pm_fwd.K = C;
+        pm_fwd.snap0 = 0;
+        // recompute pass: design-box E^{n+1} into slots 1.., the pole term into pm_hq
+        pm_rec = pf;
+        pm_rec.snap = pm_he + 3 * c->nd;
+        pm_rec.hist_dq = pm_hq;
+        pm_rec.K = C;
+        // adjoint pass: second state set, direct drive table at the gap samples
+        pm_adj = base;
+        for (int cc = 0; cc < 3; ++cc) {
+            pm_adj.E[cc] = pm_b.fld[0] + cc * cs;
+            pm_adj.H[cc] = pm_b.fld[1] + cc * cs;
+            pm_adj.En[cc] = pm_b.fld[2] + cc * cs;
+            pm_adj.Hn[cc] = pm_b.fld[3] + cc * cs;
+            for (int t = 0; t < 2; ++t) {
+                pm_adj.psiE[cc][t] = pm_b.psiE[cc][t];
+                pm_adj.psiH[cc][t] = pm_b.psiH[cc][t];
+                pm_adj.psiHn[cc][t] = pm_b.psiHn[cc][t];
+            }
+            pm_adj.Q[cc] = pm_b.Q[cc];
+        }
+        pm_adj.ctl = pm_b.ctl;
+        pm_adj.nb = 1;
+        pm_adj.src_direct = 1;
+        pm_adj.nsamp = (int)(3 * c->ngap);
+        pm_adj.src_wave = pm_drive;
+        std::memcpy(pm_adj.sb, base.gb, sizeof pm_adj.sb);
+        pm_adj.tfsf_i0 = -1;
+        pm_adj.snap = pm_ha + 3 * c->nd;
+        pm_adj.K = C;
+    }
+
+    void pm_steps(const KParams<T>& p, const StepMaps* mp, int n_from, int n_to)
+    {
+        for (int s = n_from; s < n_to; ++s) {
+            const KParams<T> q = par(p, s);
+            CK(launch_background(q, s, false, mp));
+            CK(fdtd::launch_e_design<T>(q, bucket, c->work));
+        }
+        c->tim.launches += (long long)(n_to - n_from) * (fused ? 4 : 3);
+    }
+
+    void pm_check(const int* ctl_dev, int expect)
+    {
+        int h[4];
+        CK(cudaMemcpyAsync(h, ctl_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        if (h[2] & 4) {
+            c->dead = true;
+            throw Err{FDTD_ERR_CUDA, "a TMA plane of the step kernel did not arrive within its time limit"};
+        }
+        if (h[2] & 1) {
+            c->dead = true;
+            throw Err{FDTD_ERR_UNSTABLE, "non-finite or exploding field during the run"};
+        }
+        if (h[0] != expect) throw Err{FDTD_ERR_CUDA, "device step counter " + std::to_string(h[0]) + " != " + std::to_string(expect)};
+    }
+
+    double paper_forward(int C)
+    {
+        const int M = c->d.n_steps;
+        pm_alloc(C);
+        pm_params();
+        reset_state(0);
+        CK(cudaMemsetAsync(pm_td, 0, 3 * c->ngap * sizeof(double), c->work));
+        for (int seg = 0; seg < pm_nseg; ++seg) {
+            const int n0 = seg * pm_C, n1 = std::min(M, n0 + pm_C);
+            copy_state(par(pm_fwd, n0), pm_ckpt + (size_t)seg * pm_ckpt_bytes, true);
+            pm_steps(pm_fwd, maps, n0, n1);
+            if (c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
+        }
+        pm_check(ctl, M);
+        std::vector<double> td(3 * c->ngap);
+        CK(cudaMemcpyAsync(td.data(), pm_td, td.size() * sizeof(double), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        double s = 0.0;
+        for (double v : td) s += v;
+        const double dV = c->d.dx * c->d.dx * c->d.dx;
+        pm_have_fwd = true;
+        return 0.5 * kEps0 * dV * c->dt * s;
+    }
+
+    void paper_gradient(int single, void* out, int dtype, int on_device)
+    {
+        if (!pm_have_fwd) throw Err{FDTD_ERR_STATE, "paper gradient before paper forward"};
+        pm_params();
+        const fdtd_grid_desc& d = c->d;
+        const int M = d.n_steps;
+        const size_t ns = 3 * c->ngap;
+        CK(fdtd::launch_paper_drive<T>(pm_gh, pm_drive, M, (int)ns, kEps0, c->work));
+        // adjoint state to zero
+        for (int f = 0; f < 4; ++f) CK(cudaMemsetAsync(pm_b.fld[f], 0, 3 * cs * sizeof(T), c->work));
+        for (int cc = 0; cc < 3; ++cc)
+            for (int t = 0; t < 2; ++t) {
+                const size_t m = psi_elems(cc, t);
+                if (!m) continue;
+                CK(cudaMemsetAsync(pm_b.psiE[cc][t], 0, m * sizeof(T), c->work));
+                CK(cudaMemsetAsync(pm_b.psiH[cc][t], 0, m * sizeof(T), c->work));
+                CK(cudaMemsetAsync(pm_b.psiHn[cc][t], 0, m * sizeof(T), c->work));
+            }
+        for (int cc = 0; cc < 3; ++cc)
+            if (ptot[cc]) CK(cudaMemsetAsync(pm_b.Q[cc], 0, c->nd * ptot[cc] * sizeof(cpx<T>), c->work));
+        CK(cudaMemsetAsync(pm_b.ctl, 0, 4 * sizeof(int), c->work));
+        CK(cudaMemsetAsync(pm_gsum, 0, c->nd * sizeof(double), c->work));
+        fdtd::PParams<T> g{};
+        g.nd = (long long)c->nd;
+        g.dnx = base.dnx;
+        g.dny = base.dny;
+        std::memcpy(g.db, base.db, sizeof g.db);
+        std::memcpy(g.gb, base.gb, sizeof g.gb);
+        g.he = pm_he;
+        g.ha = pm_ha;
+        g.hq = pm_hq;
+        g.rho = rho;
+        g.gsum = pm_gsum;
+        g.single = single ? 1 : 0;
+        for (int k = 0; k < 3; ++k) {
+            g.deps[k] = mat_m2.eps[k] - mat_m1.eps[k];
+            g.dsig[k] = mat_m2.sig[k] - mat_m1.sig[k];
+        }
+        g.gamma = mat_gamma;
+        g.eps0 = kEps0;
+        g.dt = c->dt;
+        for (int seg = pm_nseg - 1; seg >= 0; --seg) {
+            const int n0 = seg * pm_C, n1 = std::min(M, n0 + pm_C), len = n1 - n0, a0 = M - n1;
+            // forward recompute of the segment from its checkpoint
+            KParams<T> pr = pm_rec;
+            pr.snap0 = n0;
+            copy_state(par(pr, n0), pm_ckpt + (size_t)seg * pm_ckpt_bytes, false);
+            CK(cudaMemcpyAsync(ctl, &n0, sizeof(int), cudaMemcpyHostToDevice, c->work));
+            CK(fdtd::launch_gather_design_e<T>(par(pr, n0), pm_he, c->work));
+            pm_steps(pr, maps, n0, n1);
+            // adjoint over the mirrored steps a0 .. a0 + len
+            KParams<T> pa2 = pm_adj;
+            pa2.snap0 = a0;
+            CK(fdtd::launch_gather_design_e<T>(par(pa2, a0), pm_ha, c->work));
+            pm_steps(pa2, pm_maps, a0, a0 + len);
+            g.len = len;
+            CK(fdtd::launch_paper_grad<T>(g, c->work));
+            c->tim.launches += 3;
+            CK(cudaStreamSynchronize(c->work));      // n0 above is a host stack value read by the copy
+            if (c->cancel.load()) throw Err{FDTD_ERR_CANCELLED, "cancelled"};
+        }
+        pm_check(pm_b.ctl, M);
+        std::vector<double> gs(c->nd);
+        CK(cudaMemcpyAsync(gs.data(), pm_gsum, c->nd * sizeof(double), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        const double dV = d.dx * d.dx * d.dx;
+        for (double& v : gs) v *= dV;
+        if (!out) return;
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+        if (dtype == 1) {
+            CK(cudaMemcpyAsync(out, gs.data(), c->nd * sizeof(double), kind, c->work));
+            CK(cudaStreamSynchronize(c->work));
+        } else {
+            std::vector<float> gf(gs.begin(), gs.end());
+            CK(cudaMemcpyAsync(out, gf.data(), c->nd * sizeof(float), kind, c->work));
+            CK(cudaStreamSynchronize(c->work));
+        }
     }
 
     // Buffers that hold the state after a run of M steps.
@@ -747,6 +1035,7 @@ struct Solver : SolverBase {
 
     void set_density(const void* src, int dtype, int on_device)
     {
+        pm_have_fwd = false;
         const size_t n = c->nd;
         int* flag = ctl + 2;
         CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), c->work));
@@ -1360,6 +1649,36 @@ fdtd_status fdtd_gradient(fdtd_handle h, void* grad, size_t n, int dtype, int on
     });
 }
 
+fdtd_status fdtd_paper_forward(fdtd_handle h, int checkpoint_steps, double* F_out)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if (!h->has_rho) {
+        h->err = "paper forward before density";
+        return FDTD_ERR_STATE;
+    }
+    return guarded(h, [&] {
+        enter(h);
+        double F = 0.0;
+        dispatch(h, [&](auto* s) { F = s->paper_forward(checkpoint_steps); });
+        leave(h);
+        if (F_out) *F_out = F;
+    });
+}
+
+fdtd_status fdtd_paper_gradient(fdtd_handle h, int pole_pairing, void* grad, size_t n, int dtype, int on_device)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if ((grad && n != h->nd) || (dtype != 0 && dtype != 1) || (pole_pairing != 0 && pole_pairing != 1)) {
+        h->err = "paper gradient: buffer size/dtype or pole_pairing mismatch";
+        return FDTD_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        enter(h);
+        dispatch(h, [&](auto* s) { s->paper_gradient(pole_pairing, grad, dtype, on_device); });
+        leave(h);
+    });
+}
+
 fdtd_status fdtd_gradient_norm(fdtd_handle h, double* out)
 {
     if (fdtd_status s = check_handle(h)) return s;
@@ -1401,6 +1720,7 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     if (fdtd_status s = check_handle(h, true)) return s;
     if (!out) return FDTD_ERR_ARG;
     fdtd_timings t = h->tim;
+    t.fused_step = h->impl && h->impl->has_interior() ? 1 : 0;
     const double ts = h->d.precision == 64 ? 8.0 : 4.0;
     // algorithmic bytes per launch: every state word read once and written once
     const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);

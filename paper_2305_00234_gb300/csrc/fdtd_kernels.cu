@@ -202,6 +202,31 @@ cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaS
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_gather_design_e(const KParams<T>& p, T* out, cudaStream_t s)
+{
+    if (p.nd == 0) return cudaSuccess;
+    gather_design_e_kernel<T><<<(unsigned)((p.nd + 255) / 256), 256, 0, s>>>(p, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_paper_drive(const T* gh, T* drive, int M, int ns, double eps0, cudaStream_t s)
+{
+    const long long n = (long long)M * ns;
+    if (n == 0) return cudaSuccess;
+    paper_drive_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gh, drive, M, ns, eps0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_paper_grad(const PParams<T>& g, cudaStream_t s)
+{
+    if (g.nd == 0) return cudaSuccess;
+    paper_grad_kernel<T><<<(unsigned)((g.nd + 255) / 256), 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
 #define FDTD_INSTANTIATE(T)                                                                              \
     template cudaError_t prepare_step<T>();                                                              \
     template cudaError_t launch_step<T>(const KParams<T>&, const StepMaps&, cudaStream_t);               \
@@ -211,7 +236,10 @@ cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaS
     template cudaError_t launch_grad<T>(const GParams<T>&, unsigned, cudaStream_t);                      \
     template cudaError_t launch_rho_import<T>(const void*, int, long long, T*, int*, cudaStream_t);      \
     template cudaError_t launch_to_double<T>(const T*, long long, double*, cudaStream_t);                \
-    template cudaError_t launch_index_map<T>(const KParams<T>&, int, int32_t*, cudaStream_t);
+    template cudaError_t launch_index_map<T>(const KParams<T>&, int, int32_t*, cudaStream_t);            \
+    template cudaError_t launch_gather_design_e<T>(const KParams<T>&, T*, cudaStream_t);                  \
+    template cudaError_t launch_paper_drive<T>(const T*, T*, int, int, double, cudaStream_t);             \
+    template cudaError_t launch_paper_grad<T>(const PParams<T>&, cudaStream_t);
 
 FDTD_INSTANTIATE(float)
 FDTD_INSTANTIATE(double)

@@ -67,9 +67,12 @@ __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p)
 //   E' = (N(rho) E + drive - sum_p kappa_p Re{g_p Q_p}) / D(rho),
 //   Q_p <- Q_p + (alpha_p - 1) Q_p + beta_p (E' + E).
 // MP bounds the poles per component at compile time so the pole currents stay in registers.
+// dq (paper mode): sum_p dkappa_p/drho Re{Q_p^{n+1} - Q_p^n} of this sample (-1 for m1's poles,
+// +1 for m2's), the pole term of Eq. (Gradient_FDTD).
 template <typename T, int MP>
-__device__ __forceinline__ T design_sample(const KParams<T>& p, int c, T rho, long long dv, T e_old, T drive)
+__device__ __forceinline__ T design_sample(const KParams<T>& p, int c, T rho, long long dv, T e_old, T drive, T& dq)
 {
+    dq = T(0);
     const T one = T(1);
     const T gm = p.hg * rho * (one - rho);
     const T D = p.D1[c] + rho * p.dD[c] + gm;
@@ -102,6 +105,7 @@ __device__ __forceinline__ T design_sample(const KParams<T>& p, int c, T rho, lo
             v.re = q[pp].re + (a.re * q[pp].re - a.im * q[pp].im) + b.re * es;
             v.im = q[pp].im + (a.re * q[pp].im + a.im * q[pp].re) + b.im * es;
             Q[pp * p.nd + dv] = v;
+            dq += (pp < P1 ? -(v.re - q[pp].re) : (v.re - q[pp].re));
         }
     }
     return e_new;
@@ -111,6 +115,7 @@ template <typename T>
 __device__ __forceinline__ T point_drive(const KParams<T>& p, int i, int j, int k, int c, int n)
 {
     const long long lv = ((long long)(k - p.sb[4]) * (p.sb[3] - p.sb[2]) + (j - p.sb[2])) * (p.sb[1] - p.sb[0]) + (i - p.sb[0]);
+    if (p.src_direct) return __ldg(p.src_wave + (long long)n * p.nsamp + lv * 3 + c);
     const T* r = p.src_r + (lv * 3 + c) * p.nb;
     const T* w = p.src_wave + (long long)n * p.nb;
     T s = T(0);
@@ -174,11 +179,11 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const
             dyv += point_drive(p, i, j, k, 1, n);
             dzv += point_drive(p, i, j, k, 2, n);
         }
-        T ex, ey, ez;
+        T ex, ey, ez, dqx = T(0), dqy = T(0), dqz = T(0);
         if (design) {
-            ex = design_sample<T, MP>(p, 0, rho, dv, ex0, dxv);
-            ey = design_sample<T, MP>(p, 1, rho, dv, ey0, dyv);
-            ez = design_sample<T, MP>(p, 2, rho, dv, ez0, dzv);
+            ex = design_sample<T, MP>(p, 0, rho, dv, ex0, dxv, dqx);
+            ey = design_sample<T, MP>(p, 1, rho, dv, ey0, dyv, dqy);
+            ez = design_sample<T, MP>(p, 2, rho, dv, ez0, dzv, dqz);
         } else {
             ex = p.bg_ca[0] * ex0 + p.bg_cb[0] * dxv;
             ey = p.bg_ca[1] * ey0 + p.bg_cb[1] * dyv;
@@ -190,10 +195,26 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const
         p.En[0][id] = ex;
         p.En[1][id] = ey;
         p.En[2][id] = ez;
-        T* __restrict__ snap = p.snap + (long long)(n % p.K) * 3 * p.nd + dv;
+        const long long slot = (long long)((n - p.snap0) % p.K) * 3 * p.nd + dv;
+        T* __restrict__ snap = p.snap + slot;
         snap[0] = ex;
         snap[p.nd] = ey;
         snap[2 * p.nd] = ez;
+        if (p.hist_dq) {                  // paper mode, recompute pass
+            p.hist_dq[slot] = dqx;
+            p.hist_dq[slot + p.nd] = dqy;
+            p.hist_dq[slot + 2 * p.nd] = dqz;
+        }
+        if (p.td_acc && !design) {        // paper mode, forward pass: gap samples
+            const long long lg = (((long long)(k - p.gb[4]) * p.gny + (j - p.gb[2])) * p.gnx + (i - p.gb[0])) * 3;
+            p.td_acc[lg] += (double)ex * (double)ex;
+            p.td_acc[lg + 1] += (double)ey * (double)ey;
+            p.td_acc[lg + 2] += (double)ez * (double)ez;
+            T* gh = p.gap_hist + (long long)n * p.nsamp + lg;
+            gh[0] = ex;
+            gh[1] = ey;
+            gh[2] = ez;
+        }
         const T mag = fabs(ex) + fabs(ey) + fabs(ez);
         if (!(mag < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
@@ -305,6 +326,69 @@ __global__ void __launch_bounds__(kReduceThreads) grad_kernel(const GParams<T> g
         g.partial[gridDim.x] = t;
         *g.counter = 0;
     }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Paper mode (time-domain objective of Eq. (Objective_analyitically_enhancement) and gradient
+// Eq. (Gradient_FDTD) with checkpoint-recompute).
+// ---------------------------------------------------------------------------------------------
+// E of the current state at every design-box sample -> out[c][dv] (a history slot).
+template <typename T>
+__global__ void gather_design_e_kernel(const KParams<T> p, T* __restrict__ out)
+{
+    const long long dv = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (dv >= p.nd) return;
+    const int i = p.db[0] + (int)(dv % p.dnx), j = p.db[2] + (int)((dv / p.dnx) % p.dny), k = p.db[4] + (int)(dv / p.dplane);
+    const long long id = ((long long)k * p.ny + j) * p.nx + i;
+    out[dv] = p.E[0][id];
+    out[p.nd + dv] = p.E[1][id];
+    out[2 * p.nd + dv] = p.E[2][id];
+}
+
+// Adjoint drive of SI Eq. (AdjointSystem): the time-reversed functional derivative eps0 E at every
+// gap sample, delayed one step: drive[m][s] = eps0 E_s^{M-m-1}, E^{n+1} = gh[n][s], E^0 = 0.
+template <typename T>
+__global__ void paper_drive_kernel(const T* __restrict__ gh, T* __restrict__ drive, int M, int ns, double eps0)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)M * ns) return;
+    const int m = (int)(q / ns), s = (int)(q % ns);
+    const int n = M - m - 2;
+    drive[q] = n >= 0 ? (T)(eps0 * (double)gh[(long long)n * ns + s]) : T(0);
+}
+
+// One segment of Eq. (Gradient_FDTD) per design voxel: adjoint levels m = a0+1..a0+len pair with
+// forward levels L = M - m = n0+len-1..n0 (slot len - q for q = m - a0):
+//   g += sum_c [ -eps0 deps_c E^L (Et^m - Et^{m-1}) - (dsig_c + (1-2 rho) gamma) dt E^L (Et^m + Et^{m-1})/2
+//                + 2 sum_p dkappa_p Re{Q^L - Q^{L+1}} w ],   w = (Et^m + Et^{m-1})/2 or Et^{m-1};
+// sum_p dkappa_p Re{Q^L - Q^{L+1}} = -dq[L].  Gap voxels are skipped (gradient 0).
+template <typename T>
+__global__ void paper_grad_kernel(const PParams<T> g)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.nd) return;
+    const int i = g.db[0] + (int)(v % g.dnx), j = g.db[2] + (int)((v / g.dnx) % g.dny);
+    const int k = g.db[4] + (int)(v / ((long long)g.dnx * g.dny));
+    if (i >= g.gb[0] && i < g.gb[1] && j >= g.gb[2] && j < g.gb[3] && k >= g.gb[4] && k < g.gb[5]) return;
+    const double rho = (double)g.rho[v];
+    const long long st = 3 * g.nd;
+    double acc = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double a1 = -g.eps0 * g.deps[c], a2 = -(g.dsig[c] + (1.0 - 2.0 * rho) * g.gamma) * g.dt;
+        double t = 0.0;
+        double am = (double)g.ha[c * g.nd + v];               // Et^{a0}
+        for (int q = 1; q <= g.len; ++q) {
+            const double ap = (double)g.ha[q * st + c * g.nd + v];
+            const double e = (double)g.he[(g.len - q) * st + c * g.nd + v];
+            const double dq = (double)g.hq[(g.len - q) * st + c * g.nd + v];
+            const double avg = 0.5 * (ap + am);
+            t += a1 * e * (ap - am) + a2 * e * avg - 2.0 * dq * (g.single ? am : avg);
+            am = ap;
+        }
+        acc += t;
+    }
+    g.gsum[v] += acc;
 }
 
 }  // namespace fdtd

@@ -29,6 +29,12 @@ cudaError_t launch_rho_import(const void* src, int dtype, long long n, T* dst, i
 template <typename T>
 cudaError_t launch_to_double(const T* src, long long n, double* dst, cudaStream_t s);
 template <typename T>
+cudaError_t launch_gather_design_e(const KParams<T>& p, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_paper_drive(const T* gh, T* drive, int M, int ns, double eps0, cudaStream_t s);
+template <typename T>
+cudaError_t launch_paper_grad(const PParams<T>& g, cudaStream_t s);
+template <typename T>
 cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaStream_t s);
 
 }  // namespace fdtd

@@ -129,8 +129,15 @@ struct KParams {
     const T* rho;                // design box density
     cpx<T>* Q[3];                // pole currents [P[c]][nd]
     int K;                       // snapshot ring length (steps per DFT block)
+    int snap0;                   // step n writes its E^{n+1} snapshot to slot (n - snap0) mod K
     T* snap;                     // E snapshots of the design box [K][3][nd]
     int nb;                      // point-source basis functions (0 = none)
+    int src_direct;              // 1: the drive of source-box sample s at step n is src_wave[n * nsamp + s]
+    int nsamp;                   //    (s = local voxel * 3 + component), no basis expansion
+    // time-domain (paper-mode) recording, all null otherwise
+    double* td_acc;              // per gap sample (local voxel * 3 + c): sum over steps of (E^{n+1})^2
+    T* gap_hist;                 // [n][local gap voxel * 3 + c]: E^{n+1} of the gap samples
+    T* hist_dq;                  // [(n - snap0) mod K][3][nd]: sum_p dkappa_p/drho Re{Q_p^{n+1} - Q_p^n}
     const T* src_r;              // [(local sample)*nb + q], local sample = local voxel*3 + c
     const T* src_wave;           // [n*nb + q]
     int tfsf_i0;                 // first total-field x index, -1 = no TF/SF
@@ -179,6 +186,23 @@ struct GParams {
     float* grad32;
     double* partial;             // [gridDim.x + 1]
     unsigned* counter;
+};
+
+// Paper-mode gradient, one checkpoint segment of forward levels n0..n0+len and adjoint levels
+// a0..a0+len (a0 = M - n0 - len): Eq. (Gradient_FDTD) accumulated per design voxel.
+template <typename T>
+struct PParams {
+    long long nd;
+    int dnx, dny;
+    int db[6], gb[6];
+    const T* he;        // [len+1][3][nd] forward E, levels n0..n0+len
+    const T* ha;        // [len+1][3][nd] adjoint E, levels a0..a0+len
+    const T* hq;        // [len][3][nd] dq of forward steps n0..n0+len-1
+    const T* rho;
+    double* gsum;       // per design voxel, accumulated over segments
+    int len;
+    int single;         // pole term: 1 pairs the Q difference with one adjoint level, 0 the average of two
+    double deps[3], dsig[3], gamma, eps0, dt;
 };
 
 }  // namespace fdtd

@@ -71,6 +71,17 @@ class Problem:
         N.fdtd_gradient(self.h, out)
         return out
 
+    def paper_forward(self, checkpoint_steps=0):
+        """Time-domain energy objective of the paper (fdtd_paper_forward)."""
+        return N.fdtd_paper_forward(self.h, checkpoint_steps)
+
+    def paper_gradient(self, out=None, pole_pairing=0):
+        """The paper's history gradient by checkpoint-recompute (fdtd_paper_gradient)."""
+        if out is None:
+            out = np.zeros(self.dshape, dtype=np.float64)
+        N.fdtd_paper_gradient(self.h, out, pole_pairing)
+        return out
+
     def gradient_norm2(self):
         return N.fdtd_gradient_norm(self.h)
 
