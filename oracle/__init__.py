@@ -26,7 +26,8 @@ class _Desc(C.Structure):
                 ("freq_weights", C.POINTER(C.c_double)),
                 ("src_kind", C.c_int), ("src_comp", C.c_int), ("src_pos", C.c_int * 3),
                 ("src_f0", C.c_double), ("src_fwhm_hz", C.c_double), ("src_t0", C.c_double),
-                ("src_amp", C.c_double), ("adj_tau", C.c_double), ("src_wave", C.POINTER(C.c_double))]
+                ("src_amp", C.c_double), ("adj_tau", C.c_double), ("src_wave", C.POINTER(C.c_double)),
+                ("density_layout", C.c_int)]
 
 
 class _Mat(C.Structure):
@@ -107,6 +108,8 @@ class Oracle:
         d = _Desc()
         for key in ("nx", "ny", "nz", "n_steps", "src_kind", "src_comp"):
             setattr(d, key, int(desc[key]))
+        self.layout = int(desc.get("density_layout", 0))
+        d.density_layout = self.layout
         for key in ("dx", "courant", "cpml_m", "cpml_sigma_scale", "cpml_kappa_max", "cpml_a_max",
                     "src_f0", "src_fwhm_hz", "src_t0", "src_amp", "adj_tau"):
             setattr(d, key, float(desc[key]))
@@ -135,6 +138,14 @@ class Oracle:
         db = desc["design_box"]
         gb = desc["gap_box"]
         self.dshape = (db[5] - db[4], db[3] - db[2], db[1] - db[0]) if db[1] > db[0] else (0, 0, 0)
+        self.wshape = self.dshape          # DFT arrays: the working box
+        self.vshape = self.dshape          # design variables
+        if self.layout == 1 and db[1] > db[0]:
+            # one density per E sample: E_k spans the design voxels extended on the +l faces, l != k
+            nz, ny, nx = self.dshape
+            self.wshape = (nz + 1, ny + 1, nx + 1)
+            self.sample_shapes = [(nz + 1, ny + 1, nx), (nz + 1, ny, nx + 1), (nz, ny + 1, nx + 1)]
+            self.vshape = (sum(a * b * c for a, b, c in self.sample_shapes),)
         self.gshape = (gb[5] - gb[4], gb[3] - gb[2], gb[1] - gb[0]) if gb[1] > gb[0] else (0, 0, 0)
         self.nf = len(self._freqs)
 
@@ -175,7 +186,7 @@ class Oracle:
         self._check(self.lib.oracle_adjoint(self.h), "adjoint")
 
     def gradient(self):
-        g = np.zeros(self.dshape, dtype=np.float64)
+        g = np.zeros(self.vshape, dtype=np.float64)
         self._check(self.lib.oracle_gradient(self.h, _dptr(g), g.size), "gradient")
         return g
 
@@ -208,10 +219,10 @@ class Oracle:
         self._check(self.lib.oracle_set_field(self.h, which, _dptr(a), a.size), "set_field")
 
     def get_dft(self, adjoint=False):
-        n = 2 * self.nf * 3 * int(np.prod(self.dshape))
+        n = 2 * self.nf * 3 * int(np.prod(self.wshape))
         a = np.zeros(n, dtype=np.float64)
         self._check(self.lib.oracle_get_dft(self.h, 1 if adjoint else 0, _dptr(a), n), "get_dft")
-        return (a[0::2] + 1j * a[1::2]).reshape((self.nf, 3) + self.dshape)
+        return (a[0::2] + 1j * a[1::2]).reshape((self.nf, 3) + self.wshape)
 
     def get_source(self, which):
         M = int(self.desc["n_steps"])

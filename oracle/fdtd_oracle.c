@@ -55,9 +55,13 @@ struct oracle_ctx {
     int P[3], P1[3];          /* poles per component: m1's first (P1), then m2's */
     cplx* alpha[3];
     cplx* beta[3];
-    int dn[3];
-    size_t nd;
-    double* rho;
+    int wb[6];                /* working box: design box (layout 0), grown by one on +x,+y,+z (layout 1) */
+    int sbox[3][6];           /* per component: the voxels whose E_k sample is a design sample */
+    size_t soff[4];           /* layout 1: offsets of the components' samples in the density vector */
+    int dn[3];                /* working-box extents */
+    size_t nd;                /* working-box voxels */
+    size_t nvar;              /* design variables */
+    double* rho;              /* [nvar] */
     cplx* Q[3];               /* [nd][P[c]] */
     int gn[3];
     size_t ngap;
@@ -216,12 +220,32 @@ int oracle_create(const oracle_grid_desc* d, oracle_ctx** out)
     c->ncell = (size_t)d->nx * d->ny * d->nz;
     const int* db = d->design_box;
     const int* gb = d->gap_box;
+    if (d->density_layout != 0 && d->density_layout != 1) { fail(c, "bad density layout"); goto bad; }
+    memcpy(c->wb, db, sizeof c->wb);
+    for (int comp = 0; comp < 3; ++comp) memcpy(c->sbox[comp], db, sizeof c->sbox[comp]);
     if (!box_empty(db)) {
         for (int a = 0; a < 3; ++a)
             if (db[2 * a] < 0 || db[2 * a + 1] > c->n[a]) { fail(c, "design box outside grid"); goto bad; }
-        for (int a = 0; a < 3; ++a) c->dn[a] = db[2 * a + 1] - db[2 * a];
+        if (d->density_layout == 1) {
+            for (int a = 0; a < 3; ++a) {
+                c->wb[2 * a + 1] += 1;
+                if (c->wb[2 * a + 1] > c->n[a]) { fail(c, "design box + 1 outside grid"); goto bad; }
+                for (int comp = 0; comp < 3; ++comp)
+                    if (comp != a) c->sbox[comp][2 * a + 1] += 1;
+            }
+        }
+        for (int a = 0; a < 3; ++a) c->dn[a] = c->wb[2 * a + 1] - c->wb[2 * a];
     }
     c->nd = (size_t)c->dn[0] * c->dn[1] * c->dn[2];
+    c->nvar = c->nd;
+    if (d->density_layout == 1) {
+        c->soff[0] = 0;
+        for (int comp = 0; comp < 3; ++comp) {
+            const int* b = c->sbox[comp];
+            c->soff[comp + 1] = c->soff[comp] + (box_empty(db) ? 0 : (size_t)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]));
+        }
+        c->nvar = c->soff[3];
+    }
     if (!box_empty(gb)) {
         if (box_empty(db)) { fail(c, "gap without design box"); goto bad; }
         for (int a = 0; a < 3; ++a) {
@@ -264,7 +288,7 @@ int oracle_create(const oracle_grid_desc* d, oracle_ctx** out)
         }
     }
     for (int f = 0; f < 2; ++f) c->dft[f] = (cplx*)zalloc((size_t)d->n_freq * 3 * c->nd, sizeof(cplx));
-    c->rho = (double*)zalloc(c->nd, sizeof(double));
+    c->rho = (double*)zalloc(c->nvar, sizeof(double));
     int M = d->n_steps;
     c->src = (double*)zalloc((size_t)M, sizeof(double));
     c->einc = (double*)zalloc((size_t)M, sizeof(double));
@@ -350,7 +374,7 @@ int oracle_set_materials(oracle_ctx* c, const oracle_material* bg, const oracle_
 int oracle_set_density(oracle_ctx* c, const double* rho, size_t n)
 {
     if (!c || (!rho && n)) return 1;
-    if (n != c->nd) return fail(c, "density has %zu values, design box has %zu", n, c->nd);
+    if (n != c->nvar) return fail(c, "density has %zu values, the design has %zu", n, c->nvar);
     for (size_t v = 0; v < n; ++v)
         if (!(rho[v] >= 0.0 && rho[v] <= 1.0)) return fail(c, "density %zu out of [0,1]", v);
     memcpy(c->rho, rho, n * sizeof(double));
@@ -431,18 +455,33 @@ static int pec_fixed(const oracle_ctx* c, int comp, const int* ijk)
     return 0;
 }
 
-/* class of a voxel: 0 background, 1 design (blended), 2 gap (fixed background inside the box) */
+/* class of a voxel: 0 background, 1 in the working box (design state kept), 2 gap (fixed
+ * background inside the box) */
 static int voxel_class(const oracle_ctx* c, int i, int j, int k)
 {
-    if (c->nd == 0 || !in_box(c->g.design_box, i, j, k)) return 0;
+    if (c->nd == 0 || !in_box(c->wb, i, j, k)) return 0;
     if (c->ngap && in_box(c->g.gap_box, i, j, k)) return 2;
     return 1;
 }
 
+/* E_comp of voxel (i,j,k) is a design (blended) sample */
+static int design_sample(const oracle_ctx* c, int comp, int i, int j, int k)
+{
+    return voxel_class(c, i, j, k) == 1 && in_box(c->sbox[comp], i, j, k);
+}
+
 static size_t design_index(const oracle_ctx* c, int i, int j, int k)
 {
-    const int* b = c->g.design_box;
+    const int* b = c->wb;
     return ((size_t)(k - b[4]) * c->dn[1] + (j - b[2])) * c->dn[0] + (i - b[0]);
+}
+
+/* position of the density of design sample E_comp(i,j,k) in the density vector */
+static size_t rho_index(const oracle_ctx* c, int comp, int i, int j, int k)
+{
+    if (c->g.density_layout != 1) return design_index(c, i, j, k);
+    const int* b = c->sbox[comp];
+    return c->soff[comp] + ((size_t)(k - b[4]) * (b[3] - b[2]) + (j - b[2])) * (b[1] - b[0]) + (i - b[0]);
 }
 
 static size_t gap_index(const oracle_ctx* c, int i, int j, int k)
@@ -536,8 +575,9 @@ static void update_E(oracle_ctx* c, int n, int mode)
                     }
                     double drive = curl + point_drive(c, comp, i, j, k, n, mode, cls);
                     double* e = &c->E[comp][p];
-                    if (cls == 1)
-                        *e = design_sample_update(c, comp, c->rho[dv], &c->Q[comp][dv * (size_t)c->P[comp]], *e, drive);
+                    if (cls == 1 && design_sample(c, comp, i, j, k))
+                        *e = design_sample_update(c, comp, c->rho[rho_index(c, comp, i, j, k)],
+                                                  &c->Q[comp][dv * (size_t)c->P[comp]], *e, drive);
                     else
                         *e = background_sample_update(c, comp, *e, drive);
                 }
@@ -600,7 +640,7 @@ int oracle_step(oracle_ctx* c, int n_first, int n_count, int source_mode)
  * histories; this transform over all steps is its running-sum equivalent (no dt factor). */
 static void accumulate_dft(oracle_ctx* c, cplx* dft, int nt)
 {
-    const int* b = c->g.design_box;
+    const int* b = c->wb;
     for (int f = 0; f < c->g.n_freq; ++f) {
         cplx ph = cexp(-I * 2.0 * M_PI * c->freqs[f] * (double)nt * c->dt);
         for (int comp = 0; comp < 3; ++comp) {
@@ -794,6 +834,7 @@ static int paper_forward(oracle_ctx* c, double* F_out, double* eh, cplx* qh[3])
     if (!c->have_mat) return fail(c, "materials not set");
     if (c->nd && !c->have_rho) return fail(c, "density not set");
     if (!c->ngap) return fail(c, "paper mode needs a gap");
+    if (c->g.density_layout != 0) return fail(c, "paper mode takes one density per voxel");
     const int M = c->g.n_steps;
     oracle_reset(c);
     if (c->g.src_kind == 1) {
@@ -915,7 +956,8 @@ int oracle_paper_gradient(oracle_ctx* c, int align, double* F_out, double* grad,
  * the three terms of Eq. (Gradient_analytic) (eps_inf: first difference, sigma: average, poles:
  * first difference of Re Q, as in Eq. (Gradient_FDTD)).  With the adjoint DFT Lambda,
  *   dF/drho_v = - sum_{k owned by v} sum_f 2 Re{ dY_k/drho(w_f) Ehat_k(w_f) Lambda_k(w_f) },
- * and 0 on gap voxels (fixed air).
+ * and 0 on gap voxels (fixed air).  With one density per E sample (layout 1) the sum over k
+ * collapses to the sample's own component.
  * ------------------------------------------------------------------------------------------- */
 static cplx pair_response(cplx alpha, cplx beta, cplx z)
 {
@@ -925,17 +967,18 @@ static cplx pair_response(cplx alpha, cplx beta, cplx z)
 int oracle_gradient(oracle_ctx* c, double* grad, size_t n)
 {
     if (!c || !c->have_adj) return c ? fail(c, "gradient before adjoint") : 1;
-    if (n != c->nd) return fail(c, "gradient buffer size");
+    if (n != c->nvar) return fail(c, "gradient buffer size");
     const double dt = c->dt;
-    const int* db = c->g.design_box;
-    for (int k = db[4]; k < db[5]; ++k)
-        for (int j = db[2]; j < db[3]; ++j)
-            for (int i = db[0]; i < db[1]; ++i) {
-                size_t v = design_index(c, i, j, k);
-                if (voxel_class(c, i, j, k) != 1) { grad[v] = 0.0; continue; }
-                double rho = c->rho[v];
-                double G = 0.0;
-                for (int comp = 0; comp < 3; ++comp)
+    memset(grad, 0, n * sizeof(double));
+    for (int comp = 0; comp < 3; ++comp) {
+        const int* b = c->sbox[comp];
+        if (c->nd == 0) break;
+        for (int k = b[4]; k < b[5]; ++k)
+            for (int j = b[2]; j < b[3]; ++j)
+                for (int i = b[0]; i < b[1]; ++i) {
+                    if (!design_sample(c, comp, i, j, k)) continue;   /* gap: 0 */
+                    size_t r = rho_index(c, comp, i, j, k), v = design_index(c, i, j, k);
+                    double rho = c->rho[r];
                     for (int f = 0; f < c->g.n_freq; ++f) {
                         cplx z = cexp(I * 2.0 * M_PI * c->freqs[f] * dt);
                         cplx poles = 0.0;
@@ -947,10 +990,10 @@ int oracle_gradient(oracle_ctx* c, double* grad, size_t n)
                                    + (c->m2.sigma[comp] - c->m1.sigma[comp] + (1.0 - 2.0 * rho) * c->gamma) * dt * (z + 1.0) / 2.0
                                    + (z - 1.0) * poles) / dt;
                         size_t s = ((size_t)f * 3 + comp) * c->nd + v;
-                        G += -2.0 * creal(dY * c->dft[0][s] * c->dft[1][s]);
+                        grad[r] += -2.0 * creal(dY * c->dft[0][s] * c->dft[1][s]);
                     }
-                grad[v] = G;
-            }
+                }
+    }
     return 0;
 }
 
@@ -1018,7 +1061,7 @@ int oracle_get_index_map(oracle_ctx* c, int which, int32_t* dst, size_t n)
                         if (pml_depth(c->g.cpml[2 * a], c->g.cpml[2 * a + 1], c->n[a], u) > 0.0) v |= 1 << (3 + t);
                     }
                     if (which == 0) {
-                        v |= cls;
+                        v |= cls == 2 ? 2 : design_sample(c, comp, i, j, k);
                         if (pec_fixed(c, comp, ijk)) v |= 4;
                         if (c->g.src_kind == 0 && comp == c->g.src_comp && i == c->g.src_pos[0] &&
                             j == c->g.src_pos[1] && k == c->g.src_pos[2]) v |= 32;

@@ -21,6 +21,15 @@
  * Layout: every field array is (nz, ny, nx) with x fastest; voxel (i,j,k) owns E_x(i+1/2,j,k),
  * E_y(i,j+1/2,k), E_z(i,j,k+1/2).  Design-box arrays are (dnz, dny, dnx).  DFT arrays are
  * (F, 3, dnz, dny, dnx) complex, stored as interleaved (re, im) doubles.
+ *
+ * Density layouts.  0: one density per design voxel, shared by its three E samples.  1: one
+ * density per E sample, as the discretisation of Sec. "FDTD implementation and design export"
+ * counts them: the E_k samples lying in the closed design region are those of the voxels in the
+ * design box extended by one on each +l face with l != k, N~_k = prod_l (N_l + 1 - delta_kl) of
+ * them; the design variables are the three components' samples, concatenated (E_x, E_y, E_z),
+ * each (z, y, x) with x fastest over its own extents.  With layout 1 the DFT arrays and the
+ * design-box index map cover the design box grown by one cell on its +x, +y, +z sides; samples
+ * there outside their component's set keep the background update.  Paper mode takes layout 0.
  */
 #ifndef FDTD_ORACLE_H
 #define FDTD_ORACLE_H
@@ -52,6 +61,7 @@ typedef struct {
     double adj_tau;              /* envelope of the adjoint basis pulses (0: the source's) */
     const double* src_wave;      /* optional p(s dt/2), s = 0..2 n_steps, replacing the Gaussian pulse
                                     (copied at create) */
+    int density_layout;          /* 0: one density per design voxel; 1: one per E sample (below) */
 } oracle_grid_desc;
 
 typedef struct {

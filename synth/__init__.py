@@ -161,7 +161,7 @@ def base_desc(nx, ny, nz, *, dx=5e-9, courant=0.99 / math.sqrt(3.0), n_steps=100
             "freqs_hz": freqs, "freq_weights": w,
             "src_kind": src_kind, "src_comp": src_comp, "src_pos": list(src_pos),
             "src_f0": f0, "src_fwhm_hz": fwhm, "src_t0": 0.0, "src_amp": src_amp, "adj_tau": 0.0,
-            "src_wave": None}
+            "src_wave": None, "density_layout": 0}
 
 
 def sinc_hann_wave(n_steps, dt, f_c=576.5e12, rel_bw=0.5, lobes=3):
