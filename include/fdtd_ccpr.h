@@ -58,6 +58,16 @@ typedef enum {
  *    gradient and the coefficient precompute are FP64 in both.
  *  design_box must lie outside the CPML; gap_box inside design_box (gap voxels are fixed
  *    background material, gradient 0 there).
+ *  density_layout 0: one density per design voxel, shared by the voxel's three E samples (E_x at
+ *    (i+1/2, j, k), E_y at (i, j+1/2, k), E_z at (i, j, k+1/2)).  1: one density per E sample, the
+ *    count of Sec. "FDTD implementation and design export": component k has
+ *    N~_k = prod_l (N_l + 1 - delta_kl) samples (the design box's voxels extended by one on the +l
+ *    faces, l != k), so the design variables are N~ = N~_x + N~_y + N~_z values, the three
+ *    components' arrays concatenated, each (z, y, x) x fastest over its own extents.  With layout 1
+ *    the working box (DFTs, index map 2) is the design box grown by one cell on its +x, +y, +z
+ *    sides, and that box must lie outside the CPML; E samples of the working box outside their
+ *    component's sample set, and gap samples, take the background update.  Paper mode
+ *    (fdtd_paper_forward / fdtd_paper_gradient) takes layout 0 only.
  *  n_freq in [1, 8] objective frequencies (Hz) with weights.
  *  src_kind 0: soft point source on E_{src_comp} of voxel src_pos, drive added to (curl H) =
  *    src_amp (eps0/dt) p((n+1/2) dt);  src_kind 1: one-sided TF/SF plane wave along +x, E_z/H_y,
@@ -88,6 +98,7 @@ typedef struct {
     double src_f0, src_fwhm_hz, src_t0, src_amp;
     double adj_tau;
     const double* src_wave;
+    int density_layout;
 } fdtd_grid_desc;
 
 /* One CCPR material (Eq. (CCPRModel)): per Cartesian component k, eps_inf[k], sigma[k] (S/m)
@@ -163,7 +174,8 @@ fdtd_status fdtd_footprint_bytes(const fdtd_grid_desc* desc, const int p_total[3
 fdtd_status fdtd_set_materials(fdtd_handle h, const fdtd_ccpr_material* bg, const fdtd_ccpr_material* m1,
                                const fdtd_ccpr_material* m2, double gamma);
 
-/* Density on the design box, (dnz, dny, dnx) x fastest, n = dnx*dny*dnz values in [0, 1];
+/* Density on the design box, (dnz, dny, dnx) x fastest, n = dnx*dny*dnz values in [0, 1] (with
+ * density_layout 1: the N~ per-sample values described above; n_design of fdtd_get_info);
  * dtype 0 = float32, 1 = float64.  Values outside [0,1] or non-finite: FDTD_ERR_ARG (checked on
  * the device when on_device = 1). */
 fdtd_status fdtd_set_density(fdtd_handle h, const void* rho, size_t n, int dtype, int on_device);
@@ -185,14 +197,17 @@ fdtd_status fdtd_adjoint(fdtd_handle h);
  *   dY/drho = (1/dt)[eps0 d_eps (z-1) + (d_sigma + (1-2rho) gamma) dt (z+1)/2
  *                    + (z-1)(sum_{m2}(h+hb) - sum_{m1}(h+hb))],  z = e^{j w dt},
  *   h = beta (z+1)/(z-alpha), hb the same with conj(alpha), conj(beta); 0 on gap voxels.
- * grad: n = design voxels, dtype 0 float32 / 1 float64, host or device.  grad_norm2_out
+ * With density_layout 1 the derivative is per E sample (one component k, dY_k/drho_k), in the
+ * layout of fdtd_set_density, 0 on gap samples.
+ * grad: n = n_design (fdtd_get_info), dtype 0 float32 / 1 float64, host or device.  grad_norm2_out
  * (nullable, host) receives sum of squares (FP64). */
 fdtd_status fdtd_gradient(fdtd_handle h, void* grad, size_t n, int dtype, int on_device);
 fdtd_status fdtd_gradient_norm(fdtd_handle h, double* grad_norm2_out);
 
 /* Parity/inspection (host buffers, synchronous).
  *  fdtd_get_field: which 0..5 = Ex,Ey,Ez,Hx,Hy,Hz after the last run, n = nx*ny*nz doubles.
- *  fdtd_get_dft: adjoint 0/1, n_doubles = 2*F*3*nd, layout (F,3,dnz,dny,dnx) complex interleaved.
+ *  fdtd_get_dft: adjoint 0/1, n_doubles = 2*F*3*nd, layout (F,3,dnz,dny,dnx) complex interleaved over
+ *    the working box (see density_layout).
  *  fdtd_get_index_map: which 0: (3,nz,ny,nx) per E sample: bits 0-1 voxel class (0 background,
  *    1 design, 2 gap), bit 2 PEC-fixed, bits 3/4 inside the CPML of derivative axis (c+1)%3 /
  *    (c+2)%3 at the sample's integer position, bit 5 forward dipole sample; 1: (3,nz,ny,nx) per H
@@ -208,7 +223,8 @@ fdtd_status fdtd_set_profiling(fdtd_handle h, int on);
 fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out);
 fdtd_status fdtd_reset_timings(fdtd_handle h);
 
-/* Scalars: dt (s), design voxel count, gap voxel count, device footprint (bytes). */
+/* Scalars: dt (s), design variable count (voxels, or N~ with density_layout 1), gap voxel count,
+ * device footprint (bytes). */
 fdtd_status fdtd_get_info(fdtd_handle h, double* dt, size_t* n_design, size_t* n_gap, size_t* device_bytes);
 
 /* Request that a run in progress on another host thread stop at the next chunk boundary

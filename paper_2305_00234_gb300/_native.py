@@ -37,7 +37,8 @@ class GridDesc(C.Structure):
                 ("freq_weights", C.POINTER(C.c_double)),
                 ("src_kind", C.c_int), ("src_comp", C.c_int), ("src_pos", C.c_int * 3),
                 ("src_f0", C.c_double), ("src_fwhm_hz", C.c_double), ("src_t0", C.c_double),
-                ("src_amp", C.c_double), ("adj_tau", C.c_double), ("src_wave", C.POINTER(C.c_double))]
+                ("src_amp", C.c_double), ("adj_tau", C.c_double), ("src_wave", C.POINTER(C.c_double)),
+                ("density_layout", C.c_int)]
 
 
 class Material(C.Structure):
@@ -117,6 +118,7 @@ def make_desc(desc, keep):
     g = GridDesc()
     for key in ("nx", "ny", "nz", "n_steps", "precision", "src_kind", "src_comp"):
         setattr(g, key, int(desc[key]))
+    g.density_layout = int(desc.get("density_layout", 0))
     for key in ("dx", "courant", "cpml_m", "cpml_sigma_scale", "cpml_kappa_max", "cpml_a_max",
                 "src_f0", "src_fwhm_hz", "src_t0", "src_amp", "adj_tau"):
         setattr(g, key, float(desc[key]))

@@ -142,6 +142,34 @@ bool box_empty(const int* b) { return b[1] <= b[0] || b[3] <= b[2] || b[5] <= b[
 
 long long box_count(const int* b) { return box_empty(b) ? 0 : (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]); }
 
+// Working box of the solver: the design box, or with the per-sample density layout the design box
+// grown by one cell on its +x, +y, +z sides (the component sample boxes are inside it).
+void working_box(const fdtd_grid_desc& d, int out[6])
+{
+    std::memcpy(out, d.design_box, 6 * sizeof(int));
+    if (d.density_layout == 1 && !box_empty(out))
+        for (int a = 0; a < 3; ++a) out[2 * a + 1] += 1;
+}
+
+// Design variables: voxels (layout 0) or sum_k prod_l (N_l + 1 - delta_kl) samples (layout 1);
+// off[c] is where component c's samples start, md[c] their (x, y, z) extents.
+size_t design_vars(const fdtd_grid_desc& d, long long off[4], int md[3][3])
+{
+    const int* db = d.design_box;
+    const int N[3] = {db[1] - db[0], db[3] - db[2], db[5] - db[4]};
+    off[0] = 0;
+    for (int c = 0; c < 3; ++c) {
+        long long cnt = 1;
+        for (int a = 0; a < 3; ++a) {
+            md[c][a] = box_empty(db) ? 0 : N[a] + (d.density_layout == 1 && a != c ? 1 : 0);
+            cnt *= md[c][a];
+        }
+        off[c + 1] = off[c] + cnt;
+    }
+    if (d.density_layout != 1) return (size_t)box_count(db);
+    return (size_t)off[3];
+}
+
 void validate(const fdtd_grid_desc& d)
 {
     const int n[3] = {d.nx, d.ny, d.nz};
@@ -160,18 +188,22 @@ void validate(const fdtd_grid_desc& d)
         if (!(d.freqs_hz[f] > 0.0) || (d.freq_weights && !std::isfinite(d.freq_weights[f]))) arg_error("bad frequency/weight");
     if (!(d.cpml_m >= 0.0) || !(d.cpml_kappa_max >= 1.0) || !(d.cpml_a_max >= 0.0) || !(d.cpml_sigma_scale >= 0.0))
         arg_error("bad CPML profile parameters");
-    const int* db = d.design_box;
+    if (d.density_layout != 0 && d.density_layout != 1) arg_error("density_layout must be 0 (per voxel) or 1 (per E sample)");
+    int db[6];
+    working_box(d, db);
     const int* gb = d.gap_box;
     if (!box_empty(db)) {
         for (int a = 0; a < 3; ++a)
             if (db[2 * a] < d.cpml[2 * a] || db[2 * a + 1] > n[a] - d.cpml[2 * a + 1] || db[2 * a] >= db[2 * a + 1])
-                arg_error("design box must lie inside the grid and outside the CPML");
+                arg_error(d.density_layout == 1 ? "design box grown by one cell on its +x/+y/+z sides must lie inside the grid and outside the CPML"
+                                                : "design box must lie inside the grid and outside the CPML");
         if (box_count(db) > (1LL << 31) - 1) arg_error("design box too large");
     }
     if (!box_empty(gb)) {
         if (box_empty(db)) arg_error("gap box without a design box");
         for (int a = 0; a < 3; ++a)
-            if (gb[2 * a] < db[2 * a] || gb[2 * a + 1] > db[2 * a + 1]) arg_error("gap box must lie inside the design box");
+            if (gb[2 * a] < d.design_box[2 * a] || gb[2 * a + 1] > d.design_box[2 * a + 1])
+                arg_error("gap box must lie inside the design box");
     }
     if (d.src_kind == 0) {
         for (int a = 0; a < 3; ++a)
@@ -194,7 +226,13 @@ size_t footprint(const fdtd_grid_desc& d, const int ptot[3])
 {
     const size_t ts = d.precision == 64 ? 8 : 4;
     const size_t ncell = (size_t)d.nx * d.ny * d.nz;
-    const size_t nd = (size_t)box_count(d.design_box);
+    int wb[6];
+    working_box(d, wb);
+    const size_t nd = (size_t)box_count(wb);
+    long long off[4];
+    int md[3][3];
+    const size_t nvar = design_vars(d, off, md);
+    const size_t nv = std::max(nd, nvar);
     const size_t ng = (size_t)box_count(d.gap_box);
     const int n[3] = {d.nx, d.ny, d.nz};
     const size_t cs = (ncell + 31) / 32 * 32;
@@ -203,11 +241,11 @@ size_t footprint(const fdtd_grid_desc& d, const int ptot[3])
         const size_t w = (size_t)d.cpml[2 * a] + d.cpml[2 * a + 1];
         b += 6 * (ncell / n[a]) * w * ts + 8 * w * ts;               // psi_E, psi_H (two buffers)
     }
-    b += nd * ts;                                                     // rho
+    b += (d.density_layout == 1 ? 3 : 1) * nd * ts;                  // rho (per component with layout 1)
     for (int k = 0; k < 3; ++k) b += nd * (size_t)ptot[k] * 2 * ts;   // Q
     b += 2 * nd * 3 * (size_t)d.n_freq * 16;                          // forward + adjoint DFT
-    b += (size_t)fdtd::kMaxSnap * 3 * nd * ts + nd * 8;               // DFT snapshot ring, staging
-    b += nd * 8 + ((nd + 255) / 256 + 1) * 8;                         // gradient + partials
+    b += (size_t)fdtd::kMaxSnap * 3 * nd * ts + nv * 8;               // DFT snapshot ring, staging
+    b += nv * 8 + ((nv + 255) / 256 + 1) * 8;                         // gradient + partials
     b += ((size_t)d.n_steps + 1) * d.n_freq * 2 * ts;                 // phase table
     b += (size_t)d.n_steps * (2 * fdtd::kMaxBasis + 2) * ts;          // source waves, TF/SF tables
     b += (ng * 3 * fdtd::kMaxBasis + 3) * ts + ng * 3 * d.n_freq * 16;
@@ -275,7 +313,11 @@ struct fdtd_ctx {
     cudaEvent_t fence = nullptr, fork = nullptr, join = nullptr;
     int device = 0;
     double dt = 0;
-    size_t ncell = 0, nd = 0, ngap = 0;
+    size_t ncell = 0, nd = 0, ngap = 0;    // nd: working-box voxels
+    size_t nvar = 0;                    // design variables (nd, or the per-sample count with layout 1)
+    long long voff[4] = {0, 0, 0, 0};  // layout 1: offsets of the components' samples
+    int vdim[3][3] = {};               //           and their (x, y, z) extents
+    int dbu[6] = {0, 0, 0, 0, 0, 0};   // the caller's design box
     int dn[3] = {0, 0, 0}, gn[3] = {0, 0, 0};
     bool has_mat = false, has_rho = false, has_fwd = false, has_adj = false, has_grad = false, dead = false;
     std::string err;
@@ -430,8 +472,16 @@ struct Solver : SolverBase {
         }
         p.inv_dx = (T)(1.0 / d.dx);
         p.ch = (T)(c->dt / kMu0);
-        rho = talloc(c->nd);
+        const bool per_sample = c->d.density_layout == 1;
+        rho = talloc((per_sample ? 3 : 1) * c->nd);
         p.rho = rho;
+        for (int cc = 0; cc < 3; ++cc) {
+            p.rhoc[cc] = per_sample ? rho + cc * c->nd : rho;
+            std::memcpy(p.mb[cc], c->dbu, sizeof p.mb[cc]);
+            if (per_sample && c->nd)
+                for (int a = 0; a < 3; ++a)
+                    if (a != cc) p.mb[cc][2 * a + 1] += 1;
+        }
         poles = (PoleTable<T>*)c->alloc(sizeof(PoleTable<T>));
         CK(cudaMemsetAsync(poles, 0, sizeof(PoleTable<T>), c->work));
         p.poles = poles;
@@ -460,7 +510,7 @@ struct Solver : SolverBase {
         p.K = fdtd::kMaxSnap;
         snap = talloc((size_t)fdtd::kMaxSnap * 3 * c->nd);
         p.snap = snap;
-        staging = c->alloc(std::max<size_t>(c->nd, 1) * sizeof(double));
+        staging = c->alloc(std::max<size_t>(std::max(c->nd, c->nvar), 1) * sizeof(double));
         for (int m = 0; m < 2; ++m) {
             dp[m].nd = (long long)c->nd;
             dp[m].nf = d.n_freq;
@@ -492,8 +542,9 @@ struct Solver : SolverBase {
         src_wave[1] = talloc((size_t)d.n_steps * 2 * d.n_freq);
         src_r[1] = talloc(std::max<size_t>(c->ngap * 3 * 2 * d.n_freq, 1));
         gapbuf = (double2*)c->alloc(std::max<size_t>(c->ngap * 3 * d.n_freq, 1) * sizeof(double2));
-        grad = (double*)c->alloc(std::max<size_t>(c->nd, 1) * sizeof(double));
-        const size_t nblk = (c->nd + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads;
+        const size_t nout = std::max(c->nd, c->nvar);
+        grad = (double*)c->alloc(std::max<size_t>(nout, 1) * sizeof(double));
+        const size_t nblk = (nout + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads;
         partial = (double*)c->alloc((nblk + 1) * sizeof(double));
         counter = (unsigned*)c->alloc(sizeof(unsigned));
         CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), c->work));
@@ -806,6 +857,7 @@ struct Solver : SolverBase {
         const fdtd_grid_desc& d = c->d;
         const int M = d.n_steps;
         if (c->nd == 0 || c->ngap == 0) arg_error("paper mode needs a design box with a gap");
+        if (d.density_layout != 0) arg_error("paper mode takes one density per voxel (density_layout 0)");
         if (!pm_b.fld[0]) {                      // adjoint state set, allocated once
             for (int f = 0; f < 4; ++f) pm_b.fld[f] = talloc(3 * cs);
             for (int cc = 0; cc < 3; ++cc)
@@ -1036,7 +1088,8 @@ struct Solver : SolverBase {
     void set_density(const void* src, int dtype, int on_device)
     {
         pm_have_fwd = false;
-        const size_t n = c->nd;
+        const bool per_sample = c->d.density_layout == 1;
+        const size_t n = c->nvar;
         int* flag = ctl + 2;
         CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), c->work));
         const void* dsrc = src;
@@ -1044,7 +1097,13 @@ struct Solver : SolverBase {
             CK(cudaMemcpyAsync(staging, src, n * (dtype == 0 ? 4 : 8), cudaMemcpyHostToDevice, c->work));
             dsrc = staging;
         }
-        CK(fdtd::launch_rho_import<T>(dsrc, dtype, (long long)n, rho, flag, c->work));
+        if (per_sample) {   // compact per-component samples -> the three working-box arrays
+            CK(cudaMemsetAsync(rho, 0, 3 * c->nd * sizeof(T), c->work));
+            CK(fdtd::launch_rho_scatter<T>(dsrc, dtype, (long long)n, c->voff, c->vdim, c->dn[0], c->dn[1],
+                                           (long long)c->nd, rho, flag, c->work));
+        } else {
+            CK(fdtd::launch_rho_import<T>(dsrc, dtype, (long long)n, rho, flag, c->work));
+        }
         c->tim.launches++;
         int hflag[4];
         CK(cudaMemcpyAsync(hflag, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
@@ -1339,6 +1398,11 @@ struct Solver : SolverBase {
         g.dft_a = dft[1];
         g.AB = AB;
         g.rho = rho;
+        g.per_comp = c->d.density_layout == 1 ? 1 : 0;
+        g.nout = (long long)c->nvar;
+        std::memcpy(g.off, c->voff, sizeof g.off);
+        std::memcpy(g.mdim, c->vdim, sizeof g.mdim);
+        for (int cc = 0; cc < 3; ++cc) g.rhoc[cc] = base.rhoc[cc];
         g.grad64 = grad;
         g.grad32 = nullptr;
         float* grad32_dev = (float*)staging;
@@ -1350,7 +1414,8 @@ struct Solver : SolverBase {
         }
         g.partial = partial;
         g.counter = counter;
-        const unsigned nblk = (unsigned)((nd + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads);
+        const size_t nout = c->nvar;
+        const unsigned nblk = (unsigned)((nout + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads);
         if (nblk == 0) return;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (c->prof) {
@@ -1372,16 +1437,16 @@ struct Solver : SolverBase {
         }
         if (out && !on_device) {   // straight into the caller's (pageable or pinned) buffer
             if (dtype == 1)
-                CK(cudaMemcpyAsync(out, grad, nd * sizeof(double), cudaMemcpyDeviceToHost, c->work));
+                CK(cudaMemcpyAsync(out, grad, nout * sizeof(double), cudaMemcpyDeviceToHost, c->work));
             else
-                CK(cudaMemcpyAsync(out, grad32_dev, nd * sizeof(float), cudaMemcpyDeviceToHost, c->work));
+                CK(cudaMemcpyAsync(out, grad32_dev, nout * sizeof(float), cudaMemcpyDeviceToHost, c->work));
             CK(cudaStreamSynchronize(c->work));
         }
     }
 
     double grad_norm2()
     {
-        const unsigned nblk = (unsigned)((c->nd + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads);
+        const unsigned nblk = (unsigned)((c->nvar + fdtd::kReduceThreads - 1) / fdtd::kReduceThreads);
         double v = 0.0;
         CK(cudaMemcpyAsync(&v, partial + nblk, sizeof(double), cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
@@ -1510,6 +1575,9 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd
     fdtd_status st = guarded(c, [&] {
         validate(*desc);
         c->d = *desc;
+        std::memcpy(c->dbu, desc->design_box, sizeof c->dbu);
+        c->nvar = design_vars(*desc, c->voff, c->vdim);
+        working_box(*desc, c->d.design_box);
         c->freqs.assign(desc->freqs_hz, desc->freqs_hz + desc->n_freq);
         c->weights.assign(desc->n_freq, 1.0);
         if (desc->freq_weights) c->weights.assign(desc->freq_weights, desc->freq_weights + desc->n_freq);
@@ -1528,10 +1596,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd
         CK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
         c->dt = desc->courant * desc->dx / kC0;
         c->ncell = (size_t)desc->nx * desc->ny * desc->nz;
-        c->nd = (size_t)box_count(desc->design_box);
+        c->nd = (size_t)box_count(c->d.design_box);
         c->ngap = (size_t)box_count(desc->gap_box);
         for (int a = 0; a < 3; ++a) {
-            c->dn[a] = c->nd ? desc->design_box[2 * a + 1] - desc->design_box[2 * a] : 0;
+            c->dn[a] = c->nd ? c->d.design_box[2 * a + 1] - c->d.design_box[2 * a] : 0;
             c->gn[a] = c->ngap ? desc->gap_box[2 * a + 1] - desc->gap_box[2 * a] : 0;
         }
     });
@@ -1582,8 +1650,8 @@ fdtd_status fdtd_set_density(fdtd_handle h, const void* rho, size_t n, int dtype
         h->err = "set_materials first";
         return FDTD_ERR_STATE;
     }
-    if (n != h->nd || (dtype != 0 && dtype != 1) || (!rho && n)) {
-        h->err = "density size/dtype mismatch: expected " + std::to_string(h->nd) + " values";
+    if (n != h->nvar || (dtype != 0 && dtype != 1) || (!rho && n)) {
+        h->err = "density size/dtype mismatch: expected " + std::to_string(h->nvar) + " values";
         return FDTD_ERR_ARG;
     }
     return guarded(h, [&] {
@@ -1637,7 +1705,7 @@ fdtd_status fdtd_gradient(fdtd_handle h, void* grad, size_t n, int dtype, int on
         h->err = "gradient before adjoint";
         return FDTD_ERR_STATE;
     }
-    if ((grad && n != h->nd) || (dtype != 0 && dtype != 1)) {
+    if ((grad && n != h->nvar) || (dtype != 0 && dtype != 1)) {
         h->err = "gradient buffer size/dtype mismatch";
         return FDTD_ERR_ARG;
     }
@@ -1782,7 +1850,7 @@ fdtd_status fdtd_get_info(fdtd_handle h, double* dt, size_t* n_design, size_t* n
 {
     if (fdtd_status s = check_handle(h, true)) return s;
     if (dt) *dt = h->dt;
-    if (n_design) *n_design = h->nd;
+    if (n_design) *n_design = h->nvar;
     if (n_gap) *n_gap = h->ngap;
     if (device_bytes) *device_bytes = h->bytes;
     return FDTD_OK;

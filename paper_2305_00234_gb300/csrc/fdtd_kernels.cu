@@ -67,7 +67,7 @@ __global__ void index_map_kernel(const KParams<T> p, int which, int32_t* out)
             if (sl[a] >= 0 && tab[4 * sl[a] + 2] != T(0)) v |= 1 << (3 + t);
         }
         if (which == 0) {
-            v |= in_d ? (in_g ? 2 : 1) : 0;
+            v |= in_g ? 2 : ((in_d && in_box(p.mb[c], i, j, k)) ? 1 : 0);
             bool fixed = false;
             for (int a = 0; a < 3; ++a)
                 if (a != c && l[a] == 0) fixed = true;
@@ -227,6 +227,21 @@ cudaError_t launch_paper_grad(const PParams<T>& g, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_rho_scatter(const void* src, int dtype, long long n, const long long off[4], const int md[3][3],
+                               int dnx, int dny, long long nd, T* dst, int* flag, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int3 m0 = make_int3(md[0][0], md[0][1], md[0][2]), m1 = make_int3(md[1][0], md[1][1], md[1][2]);
+    const int3 m2 = make_int3(md[2][0], md[2][1], md[2][2]);
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (dtype == 0)
+        rho_scatter_kernel<T, float><<<nb, 256, 0, s>>>((const float*)src, n, off[1], off[2], m0, m1, m2, dnx, dny, nd, dst, flag);
+    else
+        rho_scatter_kernel<T, double><<<nb, 256, 0, s>>>((const double*)src, n, off[1], off[2], m0, m1, m2, dnx, dny, nd, dst, flag);
+    return cudaGetLastError();
+}
+
 #define FDTD_INSTANTIATE(T)                                                                              \
     template cudaError_t prepare_step<T>();                                                              \
     template cudaError_t launch_step<T>(const KParams<T>&, const StepMaps&, cudaStream_t);               \
@@ -235,6 +250,8 @@ cudaError_t launch_paper_grad(const PParams<T>& g, cudaStream_t s)
     template cudaError_t launch_dft<T>(const DParams<T>&, int, cudaStream_t);                            \
     template cudaError_t launch_grad<T>(const GParams<T>&, unsigned, cudaStream_t);                      \
     template cudaError_t launch_rho_import<T>(const void*, int, long long, T*, int*, cudaStream_t);      \
+    template cudaError_t launch_rho_scatter<T>(const void*, int, long long, const long long*, const int (*)[3], int, \
+                                               int, long long, T*, int*, cudaStream_t);                   \
     template cudaError_t launch_to_double<T>(const T*, long long, double*, cudaStream_t);                \
     template cudaError_t launch_index_map<T>(const KParams<T>&, int, int32_t*, cudaStream_t);            \
     template cudaError_t launch_gather_design_e<T>(const KParams<T>&, T*, cudaStream_t);                  \

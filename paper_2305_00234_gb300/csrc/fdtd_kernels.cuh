@@ -167,8 +167,11 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const
         const T hy_i = im ? Hy[id - 1] : T(0), hx_j = jm ? Hx[id - p.nx] : T(0);
         const T ex0 = Ex[id], ey0 = Ey[id], ez0 = Ez[id];
         const long long dv = ((long long)(k - p.db[4]) * p.dny + (j - p.db[2])) * p.dnx + (i - p.db[0]);
-        const bool design = !in_box(p.gb, i, j, k);
-        const T rho = design ? p.rho[dv] : T(0);
+        // each component is a design sample when its voxel is in that component's sample box and not
+        // in the gap; otherwise it takes the background update
+        const bool gap = in_box(p.gb, i, j, k);
+        const bool dsx = !gap && in_box(p.mb[0], i, j, k), dsy = !gap && in_box(p.mb[1], i, j, k);
+        const bool dsz = !gap && in_box(p.mb[2], i, j, k);
         const T idx = p.inv_dx;
         T dxv = ((hz - hz_j) - (hy - hy_k)) * idx;
         T dyv = ((hx - hx_k) - (hz - hz_i)) * idx;
@@ -180,15 +183,9 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const
             dzv += point_drive(p, i, j, k, 2, n);
         }
         T ex, ey, ez, dqx = T(0), dqy = T(0), dqz = T(0);
-        if (design) {
-            ex = design_sample<T, MP>(p, 0, rho, dv, ex0, dxv, dqx);
-            ey = design_sample<T, MP>(p, 1, rho, dv, ey0, dyv, dqy);
-            ez = design_sample<T, MP>(p, 2, rho, dv, ez0, dzv, dqz);
-        } else {
-            ex = p.bg_ca[0] * ex0 + p.bg_cb[0] * dxv;
-            ey = p.bg_ca[1] * ey0 + p.bg_cb[1] * dyv;
-            ez = p.bg_ca[2] * ez0 + p.bg_cb[2] * dzv;
-        }
+        ex = dsx ? design_sample<T, MP>(p, 0, p.rhoc[0][dv], dv, ex0, dxv, dqx) : p.bg_ca[0] * ex0 + p.bg_cb[0] * dxv;
+        ey = dsy ? design_sample<T, MP>(p, 1, p.rhoc[1][dv], dv, ey0, dyv, dqy) : p.bg_ca[1] * ey0 + p.bg_cb[1] * dyv;
+        ez = dsz ? design_sample<T, MP>(p, 2, p.rhoc[2][dv], dv, ez0, dzv, dqz) : p.bg_ca[2] * ez0 + p.bg_cb[2] * dzv;
         if (!(jm && km)) ex = ex0;
         if (!(km && im)) ey = ey0;
         if (!(im && jm)) ez = ez0;
@@ -205,7 +202,7 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const
             p.hist_dq[slot + p.nd] = dqy;
             p.hist_dq[slot + 2 * p.nd] = dqz;
         }
-        if (p.td_acc && !design) {        // paper mode, forward pass: gap samples
+        if (p.td_acc && gap) {            // paper mode, forward pass: gap samples
             const long long lg = (((long long)(k - p.gb[4]) * p.gny + (j - p.gb[2])) * p.gnx + (i - p.gb[0])) * 3;
             p.td_acc[lg] += (double)ex * (double)ex;
             p.td_acc[lg + 1] += (double)ey * (double)ey;
@@ -286,15 +283,25 @@ __global__ void __launch_bounds__(kReduceThreads) grad_kernel(const GParams<T> g
 {
     __shared__ double warp_part[kReduceThreads / 32];
     __shared__ bool last;
-    const long long v = (long long)blockIdx.x * kReduceThreads + threadIdx.x;
+    const long long q = (long long)blockIdx.x * kReduceThreads + threadIdx.x;
     double G = 0.0;
-    if (v < g.nd) {
+    if (q < (g.per_comp ? g.nout : g.nd)) {
+        // per voxel: v = q, the three owned samples share rho; per sample: one component c
+        long long v = q;
+        int c0 = 0, c1 = 3;
+        if (g.per_comp) {
+            c0 = q >= g.off[2] ? 2 : (q >= g.off[1] ? 1 : 0);
+            c1 = c0 + 1;
+            const long long l = q - g.off[c0];
+            const int mx = g.mdim[c0][0], my = g.mdim[c0][1];
+            v = ((l / ((long long)mx * my)) * g.dny + (l / mx) % my) * g.dnx + l % mx;
+        }
         const int i = g.db[0] + (int)(v % g.dnx);
         const int j = g.db[2] + (int)((v / g.dnx) % g.dny);
         const int k = g.db[4] + (int)(v / ((long long)g.dnx * g.dny));
         if (!in_box(g.gb, i, j, k)) {
-            const double s = 1.0 - 2.0 * (double)g.rho[v];
-            for (int c = 0; c < 3; ++c)
+            for (int c = c0; c < c1; ++c) {
+                const double s = 1.0 - 2.0 * (double)(g.per_comp ? g.rhoc[c][v] : g.rho[v]);
                 for (int f = 0; f < g.nf; ++f) {
                     const double2 A = __ldg(g.AB + (c * g.nf + f) * 2);
                     const double2 B = __ldg(g.AB + (c * g.nf + f) * 2 + 1);
@@ -304,9 +311,10 @@ __global__ void __launch_bounds__(kReduceThreads) grad_kernel(const GParams<T> g
                     const double eli_r = e.x * l.x - e.y * l.y, eli_i = e.x * l.y + e.y * l.x;
                     G -= 2.0 * (dyr * eli_r - dyi * eli_i);
                 }
+            }
         }
-        if (g.grad64) g.grad64[v] = G;
-        if (g.grad32) g.grad32[v] = (float)G;
+        if (g.grad64) g.grad64[q] = G;
+        if (g.grad32) g.grad32[q] = (float)G;
     }
     double s2 = warp_sum(G * G);
     if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = s2;
@@ -328,6 +336,23 @@ __global__ void __launch_bounds__(kReduceThreads) grad_kernel(const GParams<T> g
     }
 }
 
+
+// Per-sample density (compact: component c's samples (z, y, x) over extents md[c], components
+// concatenated) -> dst[c][dv] over the working box (dnx, dny); values checked to lie in [0, 1].
+template <typename T, typename S>
+__global__ void rho_scatter_kernel(const S* __restrict__ src, long long n, long long o1, long long o2, int3 m0, int3 m1,
+                                   int3 m2, int dnx, int dny, long long nd, T* __restrict__ dst, int* flag)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int c = q >= o2 ? 2 : (q >= o1 ? 1 : 0);
+    const int3 md = c == 0 ? m0 : (c == 1 ? m1 : m2);
+    const long long l = q - (c == 0 ? 0 : (c == 1 ? o1 : o2));
+    const long long dv = ((l / ((long long)md.x * md.y)) * dny + (l / md.x) % md.y) * dnx + l % md.x;
+    const S r = src[q];
+    if (!(r >= S(0) && r <= S(1))) atomicOr(flag, 2);
+    dst[c * nd + dv] = (T)r;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Paper mode (time-domain objective of Eq. (Objective_analyitically_enhancement) and gradient

@@ -27,6 +27,9 @@ cudaError_t launch_gap_gather(const double2* dft, long long nd, int nf, const in
 template <typename T>
 cudaError_t launch_rho_import(const void* src, int dtype, long long n, T* dst, int* flag, cudaStream_t s);
 template <typename T>
+cudaError_t launch_rho_scatter(const void* src, int dtype, long long n, const long long off[4], const int md[3][3],
+                               int dnx, int dny, long long nd, T* dst, int* flag, cudaStream_t s);
+template <typename T>
 cudaError_t launch_to_double(const T* src, long long n, double* dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gather_design_e(const KParams<T>& p, T* out, cudaStream_t s);

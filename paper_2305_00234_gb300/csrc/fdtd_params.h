@@ -127,6 +127,10 @@ struct KParams {
     int P[3], P1[3];             // poles per component (m1 first, P1 of them)
     const PoleTable<T>* poles;
     const T* rho;                // design box density
+    // per-component design samples: E_c of voxel v is blended with density rhoc[c][v] when the
+    // voxel lies in mb[c] and not in the gap (one density per voxel: rhoc[c] = rho, mb[c] = db)
+    const T* rhoc[3];
+    int mb[3][6];
     cpx<T>* Q[3];                // pole currents [P[c]][nd]
     int K;                       // snapshot ring length (steps per DFT block)
     int snap0;                   // step n writes its E^{n+1} snapshot to slot (n - snap0) mod K
@@ -182,6 +186,12 @@ struct GParams {
     const double2* dft_a;
     const double2* AB;           // [c][f][2]: A, B
     const T* rho;
+    // per-sample layout (per_comp = 1): output q in [0, nout) is sample q - off[c] of component c,
+    // (z, y, x) over extents mdim[c]; its density rhoc[c][dv] with dv its working-box voxel
+    int per_comp;
+    long long nout, off[4];
+    int mdim[3][3];
+    const T* rhoc[3];
     double* grad64;              // one of grad64 / grad32 is non-null
     float* grad32;
     double* partial;             // [gridDim.x + 1]

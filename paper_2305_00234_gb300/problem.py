@@ -13,6 +13,23 @@ def box_shape(box):
     return (box[5] - box[4], box[3] - box[2], box[1] - box[0])
 
 
+def sample_shapes(box):
+    """(z, y, x) extents of the E_x, E_y, E_z sample sets of a design box under density layout 1:
+    component k spans the box's voxels extended by one on the +l faces, l != k."""
+    nz, ny, nx = box_shape(box)
+    if nz == 0:
+        return [(0, 0, 0)] * 3
+    return [(nz + 1, ny + 1, nx), (nz + 1, ny, nx + 1), (nz, ny + 1, nx + 1)]
+
+
+def working_box(box, layout):
+    """Box the solver keeps design state on (DFTs): the design box, grown by one cell on its +x,
+    +y, +z sides under density layout 1."""
+    if layout != 1 or box_shape(box)[0] == 0:
+        return list(box)
+    return [box[0], box[1] + 1, box[2], box[3] + 1, box[4], box[5] + 1]
+
+
 class Problem:
     """One gradient problem on the current CUDA device.
 
@@ -30,10 +47,16 @@ class Problem:
             self.close()
             raise
         self.n = (int(desc["nz"]), int(desc["ny"]), int(desc["nx"]))
-        self.dshape = box_shape(desc["design_box"])
+        self.layout = int(desc.get("density_layout", 0))
+        self.wshape = box_shape(working_box(desc["design_box"], self.layout))
+        if self.layout == 1:   # design variables: the three components' samples, concatenated
+            self.dshape = (sum(int(np.prod(s)) for s in sample_shapes(desc["design_box"])),)
+        else:
+            self.dshape = box_shape(desc["design_box"])
         self.gshape = box_shape(desc["gap_box"])
         self.nf = len(desc["freqs_hz"])
-        self.nd = int(np.prod(self.dshape))
+        self.nd = int(np.prod(self.wshape))
+        self.nvar = int(np.prod(self.dshape))
         self.ngap = int(np.prod(self.gshape))
         self.poles_total = [len(m1["poles"][k]) + len(m2["poles"][k]) for k in range(3)]
 
@@ -90,7 +113,7 @@ class Problem:
 
     def dft(self, adjoint=False):
         a = N.fdtd_get_dft(self.h, adjoint, 2 * self.nf * 3 * self.nd)
-        return (a[0::2] + 1j * a[1::2]).reshape((self.nf, 3) + self.dshape)
+        return (a[0::2] + 1j * a[1::2]).reshape((self.nf, 3) + self.wshape)
 
     def index_map(self, which):
         shape = ((3,) + self.n) if which <= 1 else self.n
