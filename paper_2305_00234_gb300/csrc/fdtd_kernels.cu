@@ -108,8 +108,8 @@ unsigned shell_blocks(ShellBoxes& s)
     for (int q = 0; q < s.n; ++q) {
         const int* B = s.b[q];
         s.first[q] = t;
-        t += (unsigned)((B[1] - B[0] + kBX - 1) / kBX) * (unsigned)((B[3] - B[2] + kBY - 1) / kBY) *
-             (unsigned)((B[5] - B[4] + kShellPZ - 1) / kShellPZ);
+        const unsigned wxy = (unsigned)(B[1] - B[0]) * (unsigned)(B[3] - B[2]);
+        t += (wxy + kShellCells - 1) / kShellCells * (unsigned)((B[5] - B[4] + kShellKZ - 1) / kShellKZ);
     }
     s.first[s.n] = t;
     return t;

@@ -26,7 +26,11 @@ constexpr int kMaxSnap = 16;      // steps per blocked DFT update (snapshot ring
 #ifndef FDTD_ED_MINB
 #define FDTD_ED_MINB 4
 #endif
-constexpr int kShellPZ = FDTD_SHELL_PZ;   // z planes per thread in the shell kernels
+#ifndef FDTD_SHELL_KZ
+#define FDTD_SHELL_KZ 8
+#endif
+constexpr int kShellPZ = FDTD_SHELL_PZ;   // z planes per batch of loads in the shell kernels
+constexpr int kShellKZ = FDTD_SHELL_KZ;   // z planes per thread in the shell kernels (a multiple of kShellPZ)
 constexpr int kKC = FDTD_KC;      // z planes per block of the fused step kernel
 
 // Fused step kernel tile: kTX x kTY cells of one z plane, kTX/2 x kTY threads, each thread two

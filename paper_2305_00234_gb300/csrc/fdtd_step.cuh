@@ -468,36 +468,61 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
 }
 
 // ---- shell: per-cell kernels ----------------------------------------------------------------------
-// Block b -> box q; a block covers kShellCells consecutive cells of the box's x-y plane (x fastest,
-// so a warp reads and writes consecutive addresses even in boxes narrower than a warp) and
-// kShellPZ planes.  Returns false for the threads past the end of the box.
+// Block b -> box q; a block covers kShellCells consecutive (x, y) columns of the box (x fastest, so a
+// warp reads and writes consecutive addresses even in boxes narrower than a warp), and each thread
+// marches up to kShellKZ planes of its column in batches of kShellPZ planes whose loads are all
+// issued before any store.  The per-column set-up (box search, column coordinates, slab indices) is
+// paid once per kShellKZ planes; cell and psi offsets are 32-bit (a grid holds fewer than 2^31
+// cells) and advance by a fixed stride per plane.
 constexpr int kShellCells = kBX * kBY;
 
-__device__ __forceinline__ bool shell_cell(const ShellBoxes& s, const int*& B, int& x, int& y, int& k0)
+struct ShellCol {
+    int x, y, k0, k1;   // column, planes [k0, k1)
+};
+
+__device__ __forceinline__ bool shell_cell(const ShellBoxes& s, ShellCol& c)
 {
     int q = 0;
     while (q + 1 < s.n && blockIdx.x >= s.first[q + 1]) ++q;
-    B = s.b[q];
+    const int* B = s.b[q];
     const unsigned loc = blockIdx.x - s.first[q];
     const unsigned wx = B[1] - B[0], wxy = wx * (B[3] - B[2]);
     const unsigned chunks = (wxy + kShellCells - 1) / kShellCells;
-    const unsigned t = (loc % chunks) * kShellCells + threadIdx.y * kBX + threadIdx.x;
-    k0 = B[4] + (int)(loc / chunks) * kShellPZ;
-    x = B[0] + (int)(t % wx);
-    y = B[2] + (int)(t / wx);
+    const unsigned zc = loc / chunks;
+    const unsigned t = (loc - zc * chunks) * kShellCells + threadIdx.y * kBX + threadIdx.x;
+    const unsigned yy = t / wx;
+    c.x = B[0] + (int)(t - yy * wx);
+    c.y = B[2] + (int)yy;
+    c.k0 = B[4] + (int)zc * kShellKZ;
+    c.k1 = min(B[5], c.k0 + kShellKZ);
     return t < wxy;
+}
+
+// 32-bit psi offsets of one column: x slab ((k ny + y) W0 + sx) = k qxs + qx0, y slab
+// ((k W1 + sy) nx + x) = k qys + qy0, z slab ((sz ny + y) nx + x) = sz plane + col.
+struct PsiCol {
+    unsigned qx0, qxs, qy0, qys;
+};
+
+template <typename T>
+__device__ __forceinline__ PsiCol psi_col(const KParams<T>& p, int x, int y, int sx, int sy)
+{
+    PsiCol c;
+    c.qxs = (unsigned)p.ny * (unsigned)p.W[0];
+    c.qx0 = (unsigned)y * (unsigned)p.W[0] + (unsigned)max(sx, 0);
+    c.qys = (unsigned)p.W[1] * (unsigned)p.nx;
+    c.qy0 = (unsigned)max(sy, 0) * (unsigned)p.nx + (unsigned)x;
+    return c;
 }
 
 // psi of one cell for the six curl terms (0 outside the slabs): [0] d/dy of the x row, [1] d/dy of
 // the z row (y slab); [2] d/dz of the x row, [3] d/dz of the y row (z slab); [4] d/dx of the y row,
 // [5] d/dx of the z row (x slab).
 template <typename T>
-__device__ __forceinline__ void psi_load(const KParams<T>& p, T* const (&ps)[3][2], int x, int y, int k, int sx, int sy,
-                                         int sz, T (&v)[6])
+__device__ __forceinline__ void psi_load(T* const (&ps)[3][2], const PsiCol& pc, unsigned k, unsigned plane,
+                                         unsigned col, int sx, int sy, int sz, T (&v)[6])
 {
-    const long long q1 = sy >= 0 ? psi_index(p, x, y, k, 1, sy) : 0;
-    const long long q2 = sz >= 0 ? psi_index(p, x, y, k, 2, sz) : 0;
-    const long long q0 = sx >= 0 ? psi_index(p, x, y, k, 0, sx) : 0;
+    const unsigned q1 = k * pc.qys + pc.qy0, q2 = (unsigned)max(sz, 0) * plane + col, q0 = k * pc.qxs + pc.qx0;
     v[0] = sy >= 0 ? ps[0][0][q1] : T(0);
     v[1] = sy >= 0 ? ps[2][1][q1] : T(0);
     v[2] = sz >= 0 ? ps[0][1][q2] : T(0);
@@ -507,21 +532,21 @@ __device__ __forceinline__ void psi_load(const KParams<T>& p, T* const (&ps)[3][
 }
 
 template <typename T>
-__device__ __forceinline__ void psi_store(const KParams<T>& p, T* const (&ps)[3][2], int x, int y, int k, int sx, int sy,
-                                          int sz, const T (&v)[6])
+__device__ __forceinline__ void psi_store(T* const (&ps)[3][2], const PsiCol& pc, unsigned k, unsigned plane,
+                                          unsigned col, int sx, int sy, int sz, const T (&v)[6])
 {
     if (sy >= 0) {
-        const long long q = psi_index(p, x, y, k, 1, sy);
+        const unsigned q = k * pc.qys + pc.qy0;
         ps[0][0][q] = v[0];
         ps[2][1][q] = v[1];
     }
     if (sz >= 0) {
-        const long long q = psi_index(p, x, y, k, 2, sz);
+        const unsigned q = (unsigned)sz * plane + col;
         ps[0][1][q] = v[2];
         ps[1][0][q] = v[3];
     }
     if (sx >= 0) {
-        const long long q = psi_index(p, x, y, k, 0, sx);
+        const unsigned q = k * pc.qxs + pc.qx0;
         ps[1][1][q] = v[4];
         ps[2][0][q] = v[5];
     }
@@ -536,178 +561,196 @@ __device__ __forceinline__ T stretch_v(T d, const T* __restrict__ tab, int s, T&
     return add_rn(mul_rn(d, kinv), psi);
 }
 
-// H of the shell.  Every load of the thread's kShellPZ planes is issued before any store (the
-// buffers it writes are not the ones it reads).
+// H of the shell.  Within a batch every load is issued before any store (the buffers it writes are
+// not the ones it reads); E_x, E_y of the plane above a batch carry over as the next batch's own.
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_h_kernel(const KParams<T> p, const ShellBoxes s)
 {
     constexpr int P = kShellPZ;
-    const int* B;
-    int x, y, k0;
-    if (!shell_cell(s, B, x, y, k0)) return;
+    ShellCol cl;
+    if (!shell_cell(s, cl)) return;
+    const int x = cl.x, y = cl.y;
     const int n = read_step<T>(p.ctl);
     const T cneg = -(p.ch * p.inv_dx), idx = p.inv_dx, ch = p.ch;
     const T einc_n = p.tfsf_i0 >= 0 ? __ldg(p.einc + n) : T(0);
+    const bool tf = x == p.tfsf_i0 - 1;   // H_y here is scattered field
     const int sx = slab_index(x, p.cpl[0], p.cph[0], p.nx), sy = slab_index(y, p.cpl[1], p.cph[1], p.ny);
     const bool xp = x + 1 < p.nx, yp = y + 1 < p.ny;
-    HIn<T> a[P];
-    T ps[P][6];
-    int sz[P];
+    const unsigned nx = (unsigned)p.nx, plane = (unsigned)p.plane, col = (unsigned)y * nx + (unsigned)x;
+    const PsiCol pc = psi_col(p, x, y, sx, sy);
+    const T* __restrict__ E0 = p.E[0];
+    const T* __restrict__ E1 = p.E[1];
+    const T* __restrict__ E2 = p.E[2];
+    T exc = E0[(unsigned)cl.k0 * plane + col], eyc = E1[(unsigned)cl.k0 * plane + col];
+    for (int kb = cl.k0; kb < cl.k1; kb += P) {
+        HIn<T> a[P];
+        T ps[P][6];
+        int sz[P];
 #pragma unroll
-    for (int r = 0; r < P; ++r) {
-        const int k = k0 + r;
-        sz[r] = slab_index(k, p.cpl[2], p.cph[2], p.nz);
-        if (k >= B[5]) continue;
-        const long long id = ((long long)k * p.ny + y) * p.nx + x;
-        const bool zp = k + 1 < p.nz;
-        a[r].ex0 = p.E[0][id];
-        a[r].ey0 = p.E[1][id];
-        a[r].ez0 = p.E[2][id];
-        a[r].ezy = yp ? p.E[2][id + p.nx] : T(0);
-        a[r].exy = yp ? p.E[0][id + p.nx] : T(0);
-        a[r].ezx = xp ? p.E[2][id + 1] : T(0);
-        a[r].eyx = xp ? p.E[1][id + 1] : T(0);
-        a[r].exz = zp ? p.E[0][id + p.plane] : T(0);
-        a[r].eyz = zp ? p.E[1][id + p.plane] : T(0);
-        a[r].hox = p.H[0][id];
-        a[r].hoy = p.H[1][id];
-        a[r].hoz = p.H[2][id];
-        psi_load(p, p.psiH, x, y, k, sx, sy, sz[r], ps[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < P; ++r) {
-        const int k = k0 + r;
-        if (k >= B[5]) continue;
-        const long long id = ((long long)k * p.ny + y) * p.nx + x;
-        const HIn<T>& c = a[r];
-        T hx, hy, hz;
-        if (sx < 0 && sy < 0 && sz[r] < 0) {
-            h_cheap(c, cneg, x == p.tfsf_i0 - 1, einc_n, hx, hy, hz);
-        } else {
-            T xa = mul_rn(sub_rn(c.ezy, c.ez0), idx), xb = mul_rn(sub_rn(c.eyz, c.ey0), idx);
-            T ya = mul_rn(sub_rn(c.exz, c.ex0), idx), yb = mul_rn(sub_rn(c.ezx, c.ez0), idx);
-            T za = mul_rn(sub_rn(c.eyx, c.ey0), idx), zb = mul_rn(sub_rn(c.exy, c.ex0), idx);
-            if (x == p.tfsf_i0 - 1) yb = sub_rn(yb, mul_rn(einc_n, idx));   // H_y here is scattered field
-            if (sy >= 0) {
-                xa = stretch_v(xa, p.pmlH[1], sy, ps[r][0]);
-                zb = stretch_v(zb, p.pmlH[1], sy, ps[r][1]);
-            }
-            if (sz[r] >= 0) {
-                xb = stretch_v(xb, p.pmlH[2], sz[r], ps[r][2]);
-                ya = stretch_v(ya, p.pmlH[2], sz[r], ps[r][3]);
-            }
-            if (sx >= 0) {
-                yb = stretch_v(yb, p.pmlH[0], sx, ps[r][4]);
-                za = stretch_v(za, p.pmlH[0], sx, ps[r][5]);
-            }
-            hx = sub_rn(c.hox, mul_rn(ch, sub_rn(xa, xb)));
-            hy = sub_rn(c.hoy, mul_rn(ch, sub_rn(ya, yb)));
-            hz = sub_rn(c.hoz, mul_rn(ch, sub_rn(za, zb)));
-            psi_store(p, p.psiHn, x, y, k, sx, sy, sz[r], ps[r]);
+        for (int r = 0; r < P; ++r) {
+            const int k = kb + r;
+            sz[r] = slab_index(k, p.cpl[2], p.cph[2], p.nz);
+            if (k >= cl.k1) continue;
+            const unsigned id = (unsigned)k * plane + col;
+            const bool zp = k + 1 < p.nz;
+            a[r].ex0 = r == 0 ? exc : a[r - 1].exz;
+            a[r].ey0 = r == 0 ? eyc : a[r - 1].eyz;
+            a[r].ez0 = E2[id];
+            a[r].ezy = yp ? E2[id + nx] : T(0);
+            a[r].exy = yp ? E0[id + nx] : T(0);
+            a[r].ezx = xp ? E2[id + 1] : T(0);
+            a[r].eyx = xp ? E1[id + 1] : T(0);
+            a[r].exz = zp ? E0[id + plane] : T(0);
+            a[r].eyz = zp ? E1[id + plane] : T(0);
+            a[r].hox = p.H[0][id];
+            a[r].hoy = p.H[1][id];
+            a[r].hoz = p.H[2][id];
+            psi_load(p.psiH, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
         }
-        p.Hn[0][id] = hx;
-        p.Hn[1][id] = hy;
-        p.Hn[2][id] = hz;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            const int k = kb + r;
+            if (k >= cl.k1) continue;
+            const unsigned id = (unsigned)k * plane + col;
+            const HIn<T>& c = a[r];
+            T hx, hy, hz;
+            if (sx < 0 && sy < 0 && sz[r] < 0) {
+                h_cheap(c, cneg, tf, einc_n, hx, hy, hz);
+            } else {
+                T xa = mul_rn(sub_rn(c.ezy, c.ez0), idx), xb = mul_rn(sub_rn(c.eyz, c.ey0), idx);
+                T ya = mul_rn(sub_rn(c.exz, c.ex0), idx), yb = mul_rn(sub_rn(c.ezx, c.ez0), idx);
+                T za = mul_rn(sub_rn(c.eyx, c.ey0), idx), zb = mul_rn(sub_rn(c.exy, c.ex0), idx);
+                if (tf) yb = sub_rn(yb, mul_rn(einc_n, idx));
+                if (sy >= 0) {
+                    xa = stretch_v(xa, p.pmlH[1], sy, ps[r][0]);
+                    zb = stretch_v(zb, p.pmlH[1], sy, ps[r][1]);
+                }
+                if (sz[r] >= 0) {
+                    xb = stretch_v(xb, p.pmlH[2], sz[r], ps[r][2]);
+                    ya = stretch_v(ya, p.pmlH[2], sz[r], ps[r][3]);
+                }
+                if (sx >= 0) {
+                    yb = stretch_v(yb, p.pmlH[0], sx, ps[r][4]);
+                    za = stretch_v(za, p.pmlH[0], sx, ps[r][5]);
+                }
+                hx = sub_rn(c.hox, mul_rn(ch, sub_rn(xa, xb)));
+                hy = sub_rn(c.hoy, mul_rn(ch, sub_rn(ya, yb)));
+                hz = sub_rn(c.hoz, mul_rn(ch, sub_rn(za, zb)));
+                psi_store(p.psiHn, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
+            }
+            p.Hn[0][id] = hx;
+            p.Hn[1][id] = hy;
+            p.Hn[2][id] = hz;
+        }
+        exc = a[P - 1].exz;   // read only when plane kb + P is this thread's
+        eyc = a[P - 1].eyz;
     }
 }
 
 // E of the shell cells outside the design box, from H^{n+1/2} of the whole grid (after the interior
-// and shell H updates of the step); loads first, like the H kernel.  Owns the step advance when
-// there is no design box.
+// and shell H updates of the step); loads first within a batch, like the H kernel, with H_x, H_y of
+// the plane below a batch carried over.  Owns the step advance when there is no design box.
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_e_kernel(const KParams<T> p, const ShellBoxes s)
 {
     constexpr int P = kShellPZ;
-    const int* B;
-    int x, y, k0;
-    const bool live = shell_cell(s, B, x, y, k0);
+    ShellCol cl;
+    const bool live = shell_cell(s, cl);
     const int n = read_step<T>(p.ctl);
     if (live) {
+        const int x = cl.x, y = cl.y;
         const T hinc_n = p.tfsf_i0 >= 0 ? __ldg(p.hinc + n) : T(0);
         const bool check = (n & 15) == 0 || n + 1 == p.n_steps;
+        const bool tf = x == p.tfsf_i0;   // H_y(i0-1/2) is scattered field
         const int sx = slab_index(x, p.cpl[0], p.cph[0], p.nx), sy = slab_index(y, p.cpl[1], p.cph[1], p.ny);
-        T h[P][3], hm[P][4], e0[P][3], ps[P][6];
-        T hxb = T(0), hyb = T(0);   // H_x, H_y of the plane below the first
-        bool on[P];
-        int sz[P];
-        {
-            const long long id = ((long long)k0 * p.ny + y) * p.nx + x;
-            if (k0 > 0) {
-                hxb = p.Hn[0][id - p.plane];
-                hyb = p.Hn[1][id - p.plane];
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < P; ++r) {
-            const int k = k0 + r;
-            sz[r] = slab_index(k, p.cpl[2], p.cph[2], p.nz);
-            on[r] = k < B[5] && !in_box(p.db, x, y, k);
-            if (k >= B[5]) continue;
-            const long long id = ((long long)k * p.ny + y) * p.nx + x;
-            h[r][0] = p.Hn[0][id];
-            h[r][1] = p.Hn[1][id];
-            h[r][2] = p.Hn[2][id];
-            hm[r][0] = y > 0 ? p.Hn[2][id - p.nx] : T(0);   // H_z(y-1)
-            hm[r][1] = y > 0 ? p.Hn[0][id - p.nx] : T(0);   // H_x(y-1)
-            hm[r][2] = x > 0 ? p.Hn[2][id - 1] : T(0);      // H_z(x-1)
-            hm[r][3] = x > 0 ? p.Hn[1][id - 1] : T(0);      // H_y(x-1)
-            e0[r][0] = p.E[0][id];
-            e0[r][1] = p.E[1][id];
-            e0[r][2] = p.E[2][id];
-            psi_load(p, p.psiE, x, y, k, sx, sy, sz[r], ps[r]);
+        const unsigned nx = (unsigned)p.nx, plane = (unsigned)p.plane, col = (unsigned)y * nx + (unsigned)x;
+        const PsiCol pc = psi_col(p, x, y, sx, sy);
+        const bool in_dxy = x >= p.db[0] && x < p.db[1] && y >= p.db[2] && y < p.db[3];
+        const T* __restrict__ H0 = p.Hn[0];
+        const T* __restrict__ H1 = p.Hn[1];
+        const T* __restrict__ H2 = p.Hn[2];
+        T hxb = T(0), hyb = T(0);   // H_x, H_y of the plane below the batch
+        if (cl.k0 > 0) {
+            hxb = H0[(unsigned)(cl.k0 - 1) * plane + col];
+            hyb = H1[(unsigned)(cl.k0 - 1) * plane + col];
         }
         T emax = T(0);
+        for (int kb = cl.k0; kb < cl.k1; kb += P) {
+            T h[P][3], hm[P][4], e0[P][3], ps[P][6];
+            bool on[P];
+            int sz[P];
 #pragma unroll
-        for (int r = 0; r < P; ++r) {
-            const int k = k0 + r;
-            const T hxz = r == 0 ? hxb : h[r - 1][0], hyz = r == 0 ? hyb : h[r - 1][1];
-            if (!on[r]) continue;
-            const long long id = ((long long)k * p.ny + y) * p.nx + x;
-            const T rxa = h[r][2] - hm[r][0], rxb = h[r][1] - hyz;
-            const T rya = h[r][0] - hxz, ryb = h[r][2] - hm[r][2];
-            const T rza = h[r][1] - hm[r][3], rzb = h[r][0] - hm[r][1];
-            const bool tf = x == p.tfsf_i0;                                    // H_y(i0-1/2) is scattered field
-            const bool src = p.nb > 0 && in_box(p.sb, x, y, k);
-            T ex, ey, ez;
-            if (sx < 0 && sy < 0 && sz[r] < 0 && !src && x > 0 && y > 0 && k > 0) {
-                ex = p.bg_ca[0] * e0[r][0] + p.bg_cbi[0] * (rxa - rxb);
-                ey = p.bg_ca[1] * e0[r][1] + p.bg_cbi[1] * (rya - ryb);
-                ez = p.bg_ca[2] * e0[r][2] + p.bg_cbi[2] * ((tf ? rza - hinc_n : rza) - rzb);
-            } else {
-                const T idx = p.inv_dx;
-                T xa = rxa * idx, xb = rxb * idx, ya = rya * idx, yb = ryb * idx, za = rza * idx, zb = rzb * idx;
-                if (tf) za -= hinc_n * idx;
-                if (sy >= 0) {
-                    xa = stretch_v(xa, p.pmlE[1], sy, ps[r][0]);
-                    zb = stretch_v(zb, p.pmlE[1], sy, ps[r][1]);
-                }
-                if (sz[r] >= 0) {
-                    xb = stretch_v(xb, p.pmlE[2], sz[r], ps[r][2]);
-                    ya = stretch_v(ya, p.pmlE[2], sz[r], ps[r][3]);
-                }
-                if (sx >= 0) {
-                    yb = stretch_v(yb, p.pmlE[0], sx, ps[r][4]);
-                    za = stretch_v(za, p.pmlE[0], sx, ps[r][5]);
-                }
-                psi_store(p, p.psiE, x, y, k, sx, sy, sz[r], ps[r]);
-                T dxv = xa - xb, dyv = ya - yb, dzv = za - zb;
-                if (src) {
-                    dxv += point_drive(p, x, y, k, 0, n);
-                    dyv += point_drive(p, x, y, k, 1, n);
-                    dzv += point_drive(p, x, y, k, 2, n);
-                }
-                ex = p.bg_ca[0] * e0[r][0] + p.bg_cb[0] * dxv;
-                ey = p.bg_ca[1] * e0[r][1] + p.bg_cb[1] * dyv;
-                ez = p.bg_ca[2] * e0[r][2] + p.bg_cb[2] * dzv;
-                const bool im = x > 0, jm = y > 0, km = k > 0;
-                if (!(jm && km)) ex = e0[r][0];   // PEC walls: components tangential to a wall at index 0 stay zero
-                if (!(km && im)) ey = e0[r][1];
-                if (!(im && jm)) ez = e0[r][2];
+            for (int r = 0; r < P; ++r) {
+                const int k = kb + r;
+                sz[r] = slab_index(k, p.cpl[2], p.cph[2], p.nz);
+                on[r] = k < cl.k1 && !(in_dxy && k >= p.db[4] && k < p.db[5]);
+                if (k >= cl.k1) continue;
+                const unsigned id = (unsigned)k * plane + col;
+                h[r][0] = H0[id];
+                h[r][1] = H1[id];
+                h[r][2] = H2[id];
+                hm[r][0] = y > 0 ? H2[id - nx] : T(0);   // H_z(y-1)
+                hm[r][1] = y > 0 ? H0[id - nx] : T(0);   // H_x(y-1)
+                hm[r][2] = x > 0 ? H2[id - 1] : T(0);    // H_z(x-1)
+                hm[r][3] = x > 0 ? H1[id - 1] : T(0);    // H_y(x-1)
+                e0[r][0] = p.E[0][id];
+                e0[r][1] = p.E[1][id];
+                e0[r][2] = p.E[2][id];
+                psi_load(p.psiE, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
             }
-            p.En[0][id] = ex;
-            p.En[1][id] = ey;
-            p.En[2][id] = ez;
-            if (check) emax = fmax(emax, fabs(ex) + fabs(ey) + fabs(ez));
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+                const int k = kb + r;
+                const T hxz = r == 0 ? hxb : h[r - 1][0], hyz = r == 0 ? hyb : h[r - 1][1];
+                if (!on[r]) continue;
+                const unsigned id = (unsigned)k * plane + col;
+                const T rxa = h[r][2] - hm[r][0], rxb = h[r][1] - hyz;
+                const T rya = h[r][0] - hxz, ryb = h[r][2] - hm[r][2];
+                const T rza = h[r][1] - hm[r][3], rzb = h[r][0] - hm[r][1];
+                const bool src = p.nb > 0 && in_box(p.sb, x, y, k);
+                T ex, ey, ez;
+                if (sx < 0 && sy < 0 && sz[r] < 0 && !src && x > 0 && y > 0 && k > 0) {
+                    ex = p.bg_ca[0] * e0[r][0] + p.bg_cbi[0] * (rxa - rxb);
+                    ey = p.bg_ca[1] * e0[r][1] + p.bg_cbi[1] * (rya - ryb);
+                    ez = p.bg_ca[2] * e0[r][2] + p.bg_cbi[2] * ((tf ? rza - hinc_n : rza) - rzb);
+                } else {
+                    const T idx = p.inv_dx;
+                    T xa = rxa * idx, xb = rxb * idx, ya = rya * idx, yb = ryb * idx, za = rza * idx, zb = rzb * idx;
+                    if (tf) za -= hinc_n * idx;
+                    if (sy >= 0) {
+                        xa = stretch_v(xa, p.pmlE[1], sy, ps[r][0]);
+                        zb = stretch_v(zb, p.pmlE[1], sy, ps[r][1]);
+                    }
+                    if (sz[r] >= 0) {
+                        xb = stretch_v(xb, p.pmlE[2], sz[r], ps[r][2]);
+                        ya = stretch_v(ya, p.pmlE[2], sz[r], ps[r][3]);
+                    }
+                    if (sx >= 0) {
+                        yb = stretch_v(yb, p.pmlE[0], sx, ps[r][4]);
+                        za = stretch_v(za, p.pmlE[0], sx, ps[r][5]);
+                    }
+                    psi_store(p.psiE, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
+                    T dxv = xa - xb, dyv = ya - yb, dzv = za - zb;
+                    if (src) {
+                        dxv += point_drive(p, x, y, k, 0, n);
+                        dyv += point_drive(p, x, y, k, 1, n);
+                        dzv += point_drive(p, x, y, k, 2, n);
+                    }
+                    ex = p.bg_ca[0] * e0[r][0] + p.bg_cb[0] * dxv;
+                    ey = p.bg_ca[1] * e0[r][1] + p.bg_cb[1] * dyv;
+                    ez = p.bg_ca[2] * e0[r][2] + p.bg_cb[2] * dzv;
+                    const bool im = x > 0, jm = y > 0, km = k > 0;
+                    if (!(jm && km)) ex = e0[r][0];   // PEC walls: components tangential to a wall at index 0 stay zero
+                    if (!(km && im)) ey = e0[r][1];
+                    if (!(im && jm)) ez = e0[r][2];
+                }
+                p.En[0][id] = ex;
+                p.En[1][id] = ey;
+                p.En[2][id] = ez;
+                if (check) emax = fmax(emax, fabs(ex) + fabs(ey) + fabs(ez));
+            }
+            hxb = h[P - 1][0];   // read only when plane kb + P is this thread's
+            hyb = h[P - 1][1];
         }
         if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
