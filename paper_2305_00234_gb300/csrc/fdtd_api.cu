@@ -198,6 +198,7 @@ void validate(const fdtd_grid_desc& d)
                 arg_error(d.density_layout == 1 ? "design box grown by one cell on its +x/+y/+z sides must lie inside the grid and outside the CPML"
                                                 : "design box must lie inside the grid and outside the CPML");
         if (box_count(db) > (1LL << 31) - 1) arg_error("design box too large");
+        if (3LL * (db[5] - db[4]) > 65535) arg_error("design box spans more than 21845 z planes");
     }
     if (!box_empty(gb)) {
         if (box_empty(db)) arg_error("gap box without a design box");

@@ -132,7 +132,8 @@ cudaError_t launch_e_design(const KParams<T>& p, int bucket, cudaStream_t s)
 {
     if (p.nd == 0) return cudaSuccess;
     const dim3 b(kBX, kBY);
-    const dim3 g = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
+    const dim3 g3 = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
+    const dim3 g(g3.x, g3.y, 3 * ((g3.z + kEdZ - 1) / kEdZ));   // one block per (kEdZ planes, component)
     switch (bucket) {
     case 0: e_design_kernel<T, 0><<<g, b, 0, s>>>(p); break;
     case 4: e_design_kernel<T, 4><<<g, b, 0, s>>>(p); break;
@@ -154,7 +155,7 @@ cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s)
 unsigned design_blocks(int dnx, int dny, int dnz)
 {
     const dim3 g = grid3(dnx, dny, dnz);
-    return g.x * g.y * g.z;
+    return g.x * g.y * 3 * ((g.z + kEdZ - 1) / kEdZ);
 }
 
 template <typename T>

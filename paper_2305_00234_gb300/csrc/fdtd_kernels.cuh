@@ -66,11 +66,23 @@ __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p)
 // E update of one design sample (blended), with Q^n:
 //   E' = (N(rho) E + drive - sum_p kappa_p Re{g_p Q_p}) / D(rho),
 //   Q_p <- Q_p + (alpha_p - 1) Q_p + beta_p (E' + E).
-// MP bounds the poles per component at compile time so the pole currents stay in registers.
+// MP bounds the poles per component at compile time so the pole currents stay in registers;
+// design_load fetches them, design_update updates E and stores them back.
 // dq (paper mode): sum_p dkappa_p/drho Re{Q_p^{n+1} - Q_p^n} of this sample (-1 for m1's poles,
 // +1 for m2's), the pole term of Eq. (Gradient_FDTD).
 template <typename T, int MP>
-__device__ __forceinline__ T design_sample(const KParams<T>& p, int c, T rho, long long dv, T e_old, T drive, T& dq)
+__device__ __forceinline__ void design_load(const KParams<T>& p, int c, long long dv, cpx<T> (&q)[MP > 0 ? MP : 1])
+{
+    const int P = p.P[c];
+    const cpx<T>* __restrict__ Q = p.Q[c];
+#pragma unroll
+    for (int pp = 0; pp < MP; ++pp)
+        if (pp < P) q[pp] = Q[pp * p.nd + dv];
+}
+
+template <typename T, int MP>
+__device__ __forceinline__ T design_update(const KParams<T>& p, int c, T rho, long long dv, const cpx<T> (&q)[MP > 0 ? MP : 1],
+                                           T e_old, T drive, T& dq)
 {
     dq = T(0);
     const T one = T(1);
@@ -81,10 +93,6 @@ __device__ __forceinline__ T design_sample(const KParams<T>& p, int c, T rho, lo
     const int P = p.P[c], P1 = p.P1[c];
     cpx<T>* __restrict__ Q = p.Q[c];
     const PoleTable<T>* __restrict__ tab = p.poles;
-    cpx<T> q[MP > 0 ? MP : 1];
-#pragma unroll
-    for (int pp = 0; pp < MP; ++pp)
-        if (pp < P) q[pp] = Q[pp * p.nd + dv];
     T sq = T(0);
 #pragma unroll
     for (int pp = 0; pp < MP; ++pp) {
@@ -142,78 +150,96 @@ __device__ __forceinline__ void finish_step(int* ctl, unsigned nblocks, int n)
 }
 
 // ---------------------------------------------------------------------------------------------
-// E update inside the design box: blended CCPR update of the design voxels, background update of
-// the gap voxels, point sources, and the E snapshot for the blocked DFT.  The design box lies
-// outside the CPML, so there is no psi here.  One cell per thread; owns the step advance.
+// E update inside the working box.  A thread owns one component c of the (x, y) column of a block
+// of kEdZ planes (blockIdx.z = 3 zc + c, so the three components of a plane run in neighbouring
+// blocks and share its H in L2; the per-block set-up and step-advance bookkeeping are paid once per
+// kEdZ planes) and handles its planes kEdPZ at a time, every load of a batch (the pole currents
+// included) before any store: blended CCPR update of the design samples, background
+// update of the gap samples and of samples outside their component's sample box, point sources,
+// the E snapshot for the blocked DFT and the paper-mode records.  The working box lies outside the
+// CPML, so there is no psi here.  Owns the step advance.
 template <typename T, int MP>
-__global__ void __launch_bounds__(kBX * kBY, FDTD_ED_MINB) e_design_kernel(const KParams<T> p)
+constexpr int ed_min_blocks()
 {
+#ifdef FDTD_ED_MINB
+    return FDTD_ED_MINB;
+#else
+    return sizeof(T) == 8 ? (MP <= 4 ? 4 : (MP <= 8 ? 3 : 2)) : (MP <= 8 ? 4 : 3);
+#endif
+}
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_kernel(const KParams<T> p)
+{
+    constexpr int PZ = kEdPZ;
+    const int zc = blockIdx.z / 3, c = blockIdx.z - 3 * zc;
     const int i = p.db[0] + blockIdx.x * kBX + threadIdx.x;
     const int j = p.db[2] + blockIdx.y * kBY + threadIdx.y;
-    const int k = p.db[4] + blockIdx.z;
+    const int k0 = p.db[4] + zc * kEdZ, k1 = min(p.db[5], k0 + kEdZ);
     const int n = read_step<T>(p.ctl);
     if (i < p.db[1] && j < p.db[3]) {
-        const long long id = ((long long)k * p.ny + j) * p.nx + i;
-        const T* __restrict__ Hx = p.Hn[0];   // H^{n+1/2}, just written by the H update
-        const T* __restrict__ Hy = p.Hn[1];
-        const T* __restrict__ Hz = p.Hn[2];
-        const T* __restrict__ Ex = p.E[0];    // E^n
-        const T* __restrict__ Ey = p.E[1];
-        const T* __restrict__ Ez = p.E[2];
-        const bool im = i > 0, jm = j > 0, km = k > 0;
-        const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
-        const T hz_j = jm ? Hz[id - p.nx] : T(0), hy_k = km ? Hy[id - p.plane] : T(0);
-        const T hx_k = km ? Hx[id - p.plane] : T(0), hz_i = im ? Hz[id - 1] : T(0);
-        const T hy_i = im ? Hy[id - 1] : T(0), hx_j = jm ? Hx[id - p.nx] : T(0);
-        const T ex0 = Ex[id], ey0 = Ey[id], ez0 = Ez[id];
-        const long long dv = ((long long)(k - p.db[4]) * p.dny + (j - p.db[2])) * p.dnx + (i - p.db[0]);
-        // each component is a design sample when its voxel is in that component's sample box and not
-        // in the gap; otherwise it takes the background update
-        const bool gap = in_box(p.gb, i, j, k);
-        const bool dsx = !gap && in_box(p.mb[0], i, j, k), dsy = !gap && in_box(p.mb[1], i, j, k);
-        const bool dsz = !gap && in_box(p.mb[2], i, j, k);
-        const T idx = p.inv_dx;
-        T dxv = ((hz - hz_j) - (hy - hy_k)) * idx;
-        T dyv = ((hx - hx_k) - (hz - hz_i)) * idx;
-        T dzv = ((hy - hy_i) - (hx - hx_j)) * idx;
-        if (i == p.tfsf_i0) dzv -= __ldg(p.hinc + n) * idx;
-        if (p.nb > 0 && in_box(p.sb, i, j, k)) {
-            dxv += point_drive(p, i, j, k, 0, n);
-            dyv += point_drive(p, i, j, k, 1, n);
-            dzv += point_drive(p, i, j, k, 2, n);
+        // (curl H)_c = (Ha - Ha(la - 1)) - (Hb - Hb(lb - 1)): c = 0: Hz along y, Hy along z;
+        // c = 1: Hx along z, Hz along x; c = 2: Hy along x, Hx along y
+        const int ca = c == 0 ? 2 : c - 1, cb = c == 2 ? 0 : c + 1;
+        const unsigned oa = c == 0 ? (unsigned)p.nx : (c == 1 ? (unsigned)p.plane : 1u);
+        const unsigned ob = c == 0 ? (unsigned)p.plane : (c == 1 ? 1u : (unsigned)p.nx);
+        const T* __restrict__ Ha = p.Hn[ca];   // H^{n+1/2}, just written by the H update
+        const T* __restrict__ Hb = p.Hn[cb];
+        const T* __restrict__ Ec = p.E[c];     // E^n
+        const T* __restrict__ rc = p.rhoc[c];
+        const unsigned plane = (unsigned)p.plane, col = (unsigned)j * (unsigned)p.nx + (unsigned)i;
+        const long long dcol = (long long)(j - p.db[2]) * p.dnx + (i - p.db[0]);
+        const bool inxy_m = i >= p.mb[c][0] && i < p.mb[c][1] && j >= p.mb[c][2] && j < p.mb[c][3];
+        const bool inxy_g = i >= p.gb[0] && i < p.gb[1] && j >= p.gb[2] && j < p.gb[3];
+        const long long slot0 = (long long)((n - p.snap0) % p.K) * 3 * p.nd + c * p.nd;
+        const T hinc_n = (c == 2 && i == p.tfsf_i0) ? __ldg(p.hinc + n) * p.inv_dx : T(0);
+        T emax = T(0);
+        for (int kb = k0; kb < k1; kb += PZ) {
+            T ha[PZ], ham[PZ], hb[PZ], hbm[PZ], e0[PZ], rho[PZ];
+            cpx<T> q[PZ][MP > 0 ? MP : 1];
+            bool ds[PZ];
+#pragma unroll
+            for (int r = 0; r < PZ; ++r) {
+                const int k = kb + r;
+                ds[r] = false;
+                if (k >= k1) continue;
+                const unsigned id = (unsigned)k * plane + col;
+                const long long dv = (long long)(k - p.db[4]) * p.dplane + dcol;
+                const int la = c == 0 ? j : (c == 1 ? k : i), lb = c == 0 ? k : (c == 1 ? i : j);
+                ha[r] = Ha[id];
+                hb[r] = Hb[id];
+                ham[r] = la > 0 ? Ha[id - oa] : T(0);
+                hbm[r] = lb > 0 ? Hb[id - ob] : T(0);
+                e0[r] = Ec[id];
+                ds[r] = inxy_m && k >= p.mb[c][4] && k < p.mb[c][5] && !(inxy_g && k >= p.gb[4] && k < p.gb[5]);
+                rho[r] = ds[r] ? rc[dv] : T(0);
+                if (ds[r]) design_load<T, MP>(p, c, dv, q[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < PZ; ++r) {
+                const int k = kb + r;
+                if (k >= k1) continue;
+                const unsigned id = (unsigned)k * plane + col;
+                const long long dv = (long long)(k - p.db[4]) * p.dplane + dcol;
+                const int la = c == 0 ? j : (c == 1 ? k : i), lb = c == 0 ? k : (c == 1 ? i : j);
+                T d = ((ha[r] - ham[r]) - (hb[r] - hbm[r])) * p.inv_dx - hinc_n;
+                if (p.nb > 0 && in_box(p.sb, i, j, k)) d += point_drive(p, i, j, k, c, n);
+                T dq = T(0);
+                T e = ds[r] ? design_update<T, MP>(p, c, rho[r], dv, q[r], e0[r], d, dq) : p.bg_ca[c] * e0[r] + p.bg_cb[c] * d;
+                if (!(la > 0 && lb > 0)) e = e0[r];   // PEC walls: components tangential to a wall at index 0 stay zero
+                p.En[c][id] = e;
+                const long long slot = slot0 + dv;
+                p.snap[slot] = e;
+                if (p.hist_dq) p.hist_dq[slot] = dq;   // paper mode, recompute pass
+                if (p.td_acc && inxy_g && k >= p.gb[4] && k < p.gb[5]) {   // paper mode, forward pass: gap samples
+                    const long long lg = (((long long)(k - p.gb[4]) * p.gny + (j - p.gb[2])) * p.gnx + (i - p.gb[0])) * 3 + c;
+                    p.td_acc[lg] += (double)e * (double)e;
+                    p.gap_hist[(long long)n * p.nsamp + lg] = e;
+                }
+                emax = fmax(emax, fabs(e));
+            }
         }
-        T ex, ey, ez, dqx = T(0), dqy = T(0), dqz = T(0);
-        ex = dsx ? design_sample<T, MP>(p, 0, p.rhoc[0][dv], dv, ex0, dxv, dqx) : p.bg_ca[0] * ex0 + p.bg_cb[0] * dxv;
-        ey = dsy ? design_sample<T, MP>(p, 1, p.rhoc[1][dv], dv, ey0, dyv, dqy) : p.bg_ca[1] * ey0 + p.bg_cb[1] * dyv;
-        ez = dsz ? design_sample<T, MP>(p, 2, p.rhoc[2][dv], dv, ez0, dzv, dqz) : p.bg_ca[2] * ez0 + p.bg_cb[2] * dzv;
-        if (!(jm && km)) ex = ex0;
-        if (!(km && im)) ey = ey0;
-        if (!(im && jm)) ez = ez0;
-        p.En[0][id] = ex;
-        p.En[1][id] = ey;
-        p.En[2][id] = ez;
-        const long long slot = (long long)((n - p.snap0) % p.K) * 3 * p.nd + dv;
-        T* __restrict__ snap = p.snap + slot;
-        snap[0] = ex;
-        snap[p.nd] = ey;
-        snap[2 * p.nd] = ez;
-        if (p.hist_dq) {                  // paper mode, recompute pass
-            p.hist_dq[slot] = dqx;
-            p.hist_dq[slot + p.nd] = dqy;
-            p.hist_dq[slot + 2 * p.nd] = dqz;
-        }
-        if (p.td_acc && gap) {            // paper mode, forward pass: gap samples
-            const long long lg = (((long long)(k - p.gb[4]) * p.gny + (j - p.gb[2])) * p.gnx + (i - p.gb[0])) * 3;
-            p.td_acc[lg] += (double)ex * (double)ex;
-            p.td_acc[lg + 1] += (double)ey * (double)ey;
-            p.td_acc[lg + 2] += (double)ez * (double)ez;
-            T* gh = p.gap_hist + (long long)n * p.nsamp + lg;
-            gh[0] = ex;
-            gh[1] = ey;
-            gh[2] = ez;
-        }
-        const T mag = fabs(ex) + fabs(ey) + fabs(ez);
-        if (!(mag < p.blowup)) atomicOr(p.ctl + 2, 1);
+        if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
     finish_step(p.ctl, p.nblocks_d, n);
 }

@@ -23,12 +23,17 @@ constexpr int kMaxSnap = 16;      // steps per blocked DFT update (snapshot ring
 #ifndef FDTD_KC
 #define FDTD_KC 16
 #endif
-#ifndef FDTD_ED_MINB
-#define FDTD_ED_MINB 4
-#endif
 #ifndef FDTD_SHELL_KZ
 #define FDTD_SHELL_KZ 8
 #endif
+#ifndef FDTD_ED_Z
+#define FDTD_ED_Z 8
+#endif
+#ifndef FDTD_ED_PZ
+#define FDTD_ED_PZ 1
+#endif
+constexpr int kEdZ = FDTD_ED_Z;     // z planes per thread in the design-E kernel
+constexpr int kEdPZ = FDTD_ED_PZ;   // of which loaded per batch
 constexpr int kShellPZ = FDTD_SHELL_PZ;   // z planes per batch of loads in the shell kernels
 constexpr int kShellKZ = FDTD_SHELL_KZ;   // z planes per thread in the shell kernels (a multiple of kShellPZ)
 constexpr int kKC = FDTD_KC;      // z planes per block of the fused step kernel
