@@ -362,6 +362,7 @@ struct Solver : SolverBase {
     T* hinc = nullptr;
     T* rho = nullptr;
     PoleTable<T>* poles = nullptr;
+    PoleTable<T> htab{};            // the same table, passed by value to the design-E kernel
     double2* dft[2] = {nullptr, nullptr};
     using V2 = typename fdtd::vec2_of<T>::type;
     V2* phase = nullptr;
@@ -680,6 +681,7 @@ struct Solver : SolverBase {
         if (!(gamma >= 0.0)) arg_error("gamma must be >= 0");
         base.hg = (T)(0.5 * gamma);
         CK(cudaMemcpyAsync(poles, &tab, sizeof tab, cudaMemcpyHostToDevice, c->work));
+        htab = tab;
         CK(cudaMemcpyAsync(AB, ab.data(), ab.size() * sizeof(double2), cudaMemcpyHostToDevice, c->work));
         build_incident(bg);
         refresh_params();
@@ -944,7 +946,7 @@ struct Solver : SolverBase {
         for (int s = n_from; s < n_to; ++s) {
             const KParams<T> q = par(p, s);
             CK(launch_background(q, s, false, mp));
-            CK(fdtd::launch_e_design<T>(q, bucket, c->work));
+            CK(fdtd::launch_e_design<T>(q, htab, bucket, c->work));
         }
         c->tim.launches += (long long)(n_to - n_from) * (fused ? 4 : 3);
     }
@@ -1145,7 +1147,7 @@ struct Solver : SolverBase {
         for (int s = 0; s < steps && err == cudaSuccess; ++s) {   // graphs start at even steps
             const KParams<T> q = par(p, s);
             err = launch_background(q, s, true);
-            if (err == cudaSuccess) err = fdtd::launch_e_design<T>(q, bucket, c->work);
+            if (err == cudaSuccess) err = fdtd::launch_e_design<T>(q, htab, bucket, c->work);
         }
         if (err == cudaSuccess) err = fdtd::launch_dft<T>(dp[mode], steps, c->work);
         cudaError_t e2 = cudaStreamEndCapture(c->work, &g);
@@ -1197,7 +1199,7 @@ struct Solver : SolverBase {
                     CK(cudaEventRecord(e[2], c->work));
                     CK(fdtd::launch_shell<T>(pp, shell, true, c->work));
                     CK(cudaEventRecord(e[3], c->work));
-                    CK(fdtd::launch_e_design<T>(pp, bucket, c->work));
+                    CK(fdtd::launch_e_design<T>(pp, htab, bucket, c->work));
                     CK(cudaEventRecord(e[4], c->work));
                 }
                 CK(fdtd::launch_dft<T>(dp[mode], cnt, c->work));

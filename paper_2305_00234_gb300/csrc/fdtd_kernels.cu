@@ -128,17 +128,17 @@ cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, 
 }
 
 template <typename T>
-cudaError_t launch_e_design(const KParams<T>& p, int bucket, cudaStream_t s)
+cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bucket, cudaStream_t s)
 {
     if (p.nd == 0) return cudaSuccess;
     const dim3 b(kBX, kBY);
     const dim3 g3 = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
     const dim3 g(g3.x, g3.y, 3 * ((g3.z + kEdZ - 1) / kEdZ));   // one block per (kEdZ planes, component)
     switch (bucket) {
-    case 0: e_design_kernel<T, 0><<<g, b, 0, s>>>(p); break;
-    case 4: e_design_kernel<T, 4><<<g, b, 0, s>>>(p); break;
-    case 8: e_design_kernel<T, 8><<<g, b, 0, s>>>(p); break;
-    default: e_design_kernel<T, 16><<<g, b, 0, s>>>(p); break;
+    case 0: e_design_kernel<T, 0><<<g, b, 0, s>>>(p, tab); break;
+    case 4: e_design_kernel<T, 4><<<g, b, 0, s>>>(p, tab); break;
+    case 8: e_design_kernel<T, 8><<<g, b, 0, s>>>(p, tab); break;
+    default: e_design_kernel<T, 16><<<g, b, 0, s>>>(p, tab); break;
     }
     return cudaGetLastError();
 }
@@ -247,7 +247,7 @@ cudaError_t launch_rho_scatter(const void* src, int dtype, long long n, const lo
     template cudaError_t prepare_step<T>();                                                              \
     template cudaError_t launch_step<T>(const KParams<T>&, const StepMaps&, cudaStream_t);               \
     template cudaError_t launch_shell<T>(const KParams<T>&, const ShellBoxes&, bool, cudaStream_t);      \
-    template cudaError_t launch_e_design<T>(const KParams<T>&, int, cudaStream_t);                       \
+    template cudaError_t launch_e_design<T>(const KParams<T>&, const PoleTable<T>&, int, cudaStream_t);                       \
     template cudaError_t launch_dft<T>(const DParams<T>&, int, cudaStream_t);                            \
     template cudaError_t launch_grad<T>(const GParams<T>&, unsigned, cudaStream_t);                      \
     template cudaError_t launch_rho_import<T>(const void*, int, long long, T*, int*, cudaStream_t);      \

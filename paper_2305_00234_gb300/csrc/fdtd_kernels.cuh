@@ -63,42 +63,43 @@ __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p)
     return v;
 }
 
-// E update of one design sample (blended), with Q^n:
+// E update of one design sample of component C (blended), with Q^n:
 //   E' = (N(rho) E + drive - sum_p kappa_p Re{g_p Q_p}) / D(rho),
 //   Q_p <- Q_p + (alpha_p - 1) Q_p + beta_p (E' + E).
 // MP bounds the poles per component at compile time so the pole currents stay in registers;
-// design_load fetches them, design_update updates E and stores them back.
+// design_load fetches them, design_update updates E and stores them back.  The pole coefficients
+// come in the kernel's parameter space (C and the pole index are compile-time, so they are
+// constant-bank operands).
 // dq (paper mode): sum_p dkappa_p/drho Re{Q_p^{n+1} - Q_p^n} of this sample (-1 for m1's poles,
 // +1 for m2's), the pole term of Eq. (Gradient_FDTD).
-template <typename T, int MP>
-__device__ __forceinline__ void design_load(const KParams<T>& p, int c, long long dv, cpx<T> (&q)[MP > 0 ? MP : 1])
+template <typename T, int MP, int C>
+__device__ __forceinline__ void design_load(const KParams<T>& p, long long dv, cpx<T> (&q)[MP > 0 ? MP : 1])
 {
-    const int P = p.P[c];
-    const cpx<T>* __restrict__ Q = p.Q[c];
+    const int P = p.P[C];
+    const cpx<T>* __restrict__ Q = p.Q[C];
 #pragma unroll
     for (int pp = 0; pp < MP; ++pp)
         if (pp < P) q[pp] = Q[pp * p.nd + dv];
 }
 
-template <typename T, int MP>
-__device__ __forceinline__ T design_update(const KParams<T>& p, int c, T rho, long long dv, const cpx<T> (&q)[MP > 0 ? MP : 1],
-                                           T e_old, T drive, T& dq)
+template <typename T, int MP, int C>
+__device__ __forceinline__ T design_update(const KParams<T>& p, const PoleTable<T>& tab, T rho, long long dv,
+                                           const cpx<T> (&q)[MP > 0 ? MP : 1], T e_old, T drive, T& dq)
 {
     dq = T(0);
     const T one = T(1);
     const T gm = p.hg * rho * (one - rho);
-    const T D = p.D1[c] + rho * p.dD[c] + gm;
-    const T N = p.N1[c] + rho * p.dN[c] - gm;
+    const T D = p.D1[C] + rho * p.dD[C] + gm;
+    const T N = p.N1[C] + rho * p.dN[C] - gm;
     if (MP == 0) return (N * e_old + drive) / D;
-    const int P = p.P[c], P1 = p.P1[c];
-    cpx<T>* __restrict__ Q = p.Q[c];
-    const PoleTable<T>* __restrict__ tab = p.poles;
+    const int P = p.P[C], P1 = p.P1[C];
+    cpx<T>* __restrict__ Q = p.Q[C];
     T sq = T(0);
 #pragma unroll
     for (int pp = 0; pp < MP; ++pp) {
         if (pp < P) {
             const T kap = pp < P1 ? one - rho : rho;
-            const cpx<T> g = ldg_c(&tab->g[c][pp]);
+            const cpx<T> g = tab.g[C][pp];
             sq += kap * (g.re * q[pp].re - g.im * q[pp].im);
         }
     }
@@ -107,8 +108,8 @@ __device__ __forceinline__ T design_update(const KParams<T>& p, int c, T rho, lo
 #pragma unroll
     for (int pp = 0; pp < MP; ++pp) {
         if (pp < P) {
-            const cpx<T> a = ldg_c(&tab->am1[c][pp]);
-            const cpx<T> b = ldg_c(&tab->beta[c][pp]);
+            const cpx<T> a = tab.am1[C][pp];
+            const cpx<T> b = tab.beta[C][pp];
             cpx<T> v;
             v.re = q[pp].re + (a.re * q[pp].re - a.im * q[pp].im) + b.re * es;
             v.im = q[pp].im + (a.re * q[pp].im + a.im * q[pp].re) + b.im * es;
@@ -164,81 +165,91 @@ constexpr int ed_min_blocks()
 #ifdef FDTD_ED_MINB
     return FDTD_ED_MINB;
 #else
-    return sizeof(T) == 8 ? (MP <= 4 ? 4 : (MP <= 8 ? 3 : 2)) : (MP <= 8 ? 4 : 3);
+    return sizeof(T) == 8 ? (MP <= 4 ? 4 : (MP <= 8 ? 3 : 2)) : (MP <= 4 ? 5 : (MP <= 8 ? 4 : 3));
 #endif
 }
 
-template <typename T, int MP>
-__global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_kernel(const KParams<T> p)
+// One component C of the (x, y) column (i, j), planes [k0, k1); returns max |E| of its samples.
+template <typename T, int MP, int C>
+__device__ __forceinline__ T e_design_column(const KParams<T>& p, const PoleTable<T>& tab, int i, int j, int k0, int k1, int n)
 {
     constexpr int PZ = kEdPZ;
+    // (curl H)_C = (Ha - Ha(la - 1)) - (Hb - Hb(lb - 1)): C = 0: Hz along y, Hy along z;
+    // C = 1: Hx along z, Hz along x; C = 2: Hy along x, Hx along y
+    constexpr int ca = C == 0 ? 2 : C - 1, cb = C == 2 ? 0 : C + 1;
+    const unsigned oa = C == 0 ? (unsigned)p.nx : (C == 1 ? (unsigned)p.plane : 1u);
+    const unsigned ob = C == 0 ? (unsigned)p.plane : (C == 1 ? 1u : (unsigned)p.nx);
+    const T* __restrict__ Ha = p.Hn[ca];   // H^{n+1/2}, just written by the H update
+    const T* __restrict__ Hb = p.Hn[cb];
+    const T* __restrict__ Ec = p.E[C];     // E^n
+    const T* __restrict__ rc = p.rhoc[C];
+    const unsigned plane = (unsigned)p.plane, col = (unsigned)j * (unsigned)p.nx + (unsigned)i;
+    const long long dcol = (long long)(j - p.db[2]) * p.dnx + (i - p.db[0]);
+    const bool inxy_m = i >= p.mb[C][0] && i < p.mb[C][1] && j >= p.mb[C][2] && j < p.mb[C][3];
+    const bool inxy_g = i >= p.gb[0] && i < p.gb[1] && j >= p.gb[2] && j < p.gb[3];
+    const long long slot0 = (long long)((n - p.snap0) % p.K) * 3 * p.nd + C * p.nd;
+    const T hinc_n = (C == 2 && i == p.tfsf_i0) ? __ldg(p.hinc + n) * p.inv_dx : T(0);
+    T emax = T(0);
+    for (int kb = k0; kb < k1; kb += PZ) {
+        T ha[PZ], ham[PZ], hb[PZ], hbm[PZ], e0[PZ], rho[PZ];
+        cpx<T> q[PZ][MP > 0 ? MP : 1];
+        bool ds[PZ];
+#pragma unroll
+        for (int r = 0; r < PZ; ++r) {
+            const int k = kb + r;
+            ds[r] = false;
+            if (k >= k1) continue;
+            const unsigned id = (unsigned)k * plane + col;
+            const long long dv = (long long)(k - p.db[4]) * p.dplane + dcol;
+            const int la = C == 0 ? j : (C == 1 ? k : i), lb = C == 0 ? k : (C == 1 ? i : j);
+            ha[r] = Ha[id];
+            hb[r] = Hb[id];
+            ham[r] = la > 0 ? Ha[id - oa] : T(0);
+            hbm[r] = lb > 0 ? Hb[id - ob] : T(0);
+            e0[r] = Ec[id];
+            ds[r] = inxy_m && k >= p.mb[C][4] && k < p.mb[C][5] && !(inxy_g && k >= p.gb[4] && k < p.gb[5]);
+            rho[r] = ds[r] ? rc[dv] : T(0);
+            if (ds[r]) design_load<T, MP, C>(p, dv, q[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < PZ; ++r) {
+            const int k = kb + r;
+            if (k >= k1) continue;
+            const unsigned id = (unsigned)k * plane + col;
+            const long long dv = (long long)(k - p.db[4]) * p.dplane + dcol;
+            const int la = C == 0 ? j : (C == 1 ? k : i), lb = C == 0 ? k : (C == 1 ? i : j);
+            T d = ((ha[r] - ham[r]) - (hb[r] - hbm[r])) * p.inv_dx - hinc_n;
+            if (p.nb > 0 && in_box(p.sb, i, j, k)) d += point_drive(p, i, j, k, C, n);
+            T dq = T(0);
+            T e = ds[r] ? design_update<T, MP, C>(p, tab, rho[r], dv, q[r], e0[r], d, dq) : p.bg_ca[C] * e0[r] + p.bg_cb[C] * d;
+            if (!(la > 0 && lb > 0)) e = e0[r];   // PEC walls: components tangential to a wall at index 0 stay zero
+            p.En[C][id] = e;
+            const long long slot = slot0 + dv;
+            p.snap[slot] = e;
+            if (p.hist_dq) p.hist_dq[slot] = dq;   // paper mode, recompute pass
+            if (p.td_acc && inxy_g && k >= p.gb[4] && k < p.gb[5]) {   // paper mode, forward pass: gap samples
+                const long long lg = (((long long)(k - p.gb[4]) * p.gny + (j - p.gb[2])) * p.gnx + (i - p.gb[0])) * 3 + C;
+                p.td_acc[lg] += (double)e * (double)e;
+                p.gap_hist[(long long)n * p.nsamp + lg] = e;
+            }
+            emax = fmax(emax, fabs(e));
+        }
+    }
+    return emax;
+}
+
+template <typename T, int MP>
+__global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_kernel(const KParams<T> p, const PoleTable<T> tab)
+{
     const int zc = blockIdx.z / 3, c = blockIdx.z - 3 * zc;
     const int i = p.db[0] + blockIdx.x * kBX + threadIdx.x;
     const int j = p.db[2] + blockIdx.y * kBY + threadIdx.y;
     const int k0 = p.db[4] + zc * kEdZ, k1 = min(p.db[5], k0 + kEdZ);
     const int n = read_step<T>(p.ctl);
     if (i < p.db[1] && j < p.db[3]) {
-        // (curl H)_c = (Ha - Ha(la - 1)) - (Hb - Hb(lb - 1)): c = 0: Hz along y, Hy along z;
-        // c = 1: Hx along z, Hz along x; c = 2: Hy along x, Hx along y
-        const int ca = c == 0 ? 2 : c - 1, cb = c == 2 ? 0 : c + 1;
-        const unsigned oa = c == 0 ? (unsigned)p.nx : (c == 1 ? (unsigned)p.plane : 1u);
-        const unsigned ob = c == 0 ? (unsigned)p.plane : (c == 1 ? 1u : (unsigned)p.nx);
-        const T* __restrict__ Ha = p.Hn[ca];   // H^{n+1/2}, just written by the H update
-        const T* __restrict__ Hb = p.Hn[cb];
-        const T* __restrict__ Ec = p.E[c];     // E^n
-        const T* __restrict__ rc = p.rhoc[c];
-        const unsigned plane = (unsigned)p.plane, col = (unsigned)j * (unsigned)p.nx + (unsigned)i;
-        const long long dcol = (long long)(j - p.db[2]) * p.dnx + (i - p.db[0]);
-        const bool inxy_m = i >= p.mb[c][0] && i < p.mb[c][1] && j >= p.mb[c][2] && j < p.mb[c][3];
-        const bool inxy_g = i >= p.gb[0] && i < p.gb[1] && j >= p.gb[2] && j < p.gb[3];
-        const long long slot0 = (long long)((n - p.snap0) % p.K) * 3 * p.nd + c * p.nd;
-        const T hinc_n = (c == 2 && i == p.tfsf_i0) ? __ldg(p.hinc + n) * p.inv_dx : T(0);
-        T emax = T(0);
-        for (int kb = k0; kb < k1; kb += PZ) {
-            T ha[PZ], ham[PZ], hb[PZ], hbm[PZ], e0[PZ], rho[PZ];
-            cpx<T> q[PZ][MP > 0 ? MP : 1];
-            bool ds[PZ];
-#pragma unroll
-            for (int r = 0; r < PZ; ++r) {
-                const int k = kb + r;
-                ds[r] = false;
-                if (k >= k1) continue;
-                const unsigned id = (unsigned)k * plane + col;
-                const long long dv = (long long)(k - p.db[4]) * p.dplane + dcol;
-                const int la = c == 0 ? j : (c == 1 ? k : i), lb = c == 0 ? k : (c == 1 ? i : j);
-                ha[r] = Ha[id];
-                hb[r] = Hb[id];
-                ham[r] = la > 0 ? Ha[id - oa] : T(0);
-                hbm[r] = lb > 0 ? Hb[id - ob] : T(0);
-                e0[r] = Ec[id];
-                ds[r] = inxy_m && k >= p.mb[c][4] && k < p.mb[c][5] && !(inxy_g && k >= p.gb[4] && k < p.gb[5]);
-                rho[r] = ds[r] ? rc[dv] : T(0);
-                if (ds[r]) design_load<T, MP>(p, c, dv, q[r]);
-            }
-#pragma unroll
-            for (int r = 0; r < PZ; ++r) {
-                const int k = kb + r;
-                if (k >= k1) continue;
-                const unsigned id = (unsigned)k * plane + col;
-                const long long dv = (long long)(k - p.db[4]) * p.dplane + dcol;
-                const int la = c == 0 ? j : (c == 1 ? k : i), lb = c == 0 ? k : (c == 1 ? i : j);
-                T d = ((ha[r] - ham[r]) - (hb[r] - hbm[r])) * p.inv_dx - hinc_n;
-                if (p.nb > 0 && in_box(p.sb, i, j, k)) d += point_drive(p, i, j, k, c, n);
-                T dq = T(0);
-                T e = ds[r] ? design_update<T, MP>(p, c, rho[r], dv, q[r], e0[r], d, dq) : p.bg_ca[c] * e0[r] + p.bg_cb[c] * d;
-                if (!(la > 0 && lb > 0)) e = e0[r];   // PEC walls: components tangential to a wall at index 0 stay zero
-                p.En[c][id] = e;
-                const long long slot = slot0 + dv;
-                p.snap[slot] = e;
-                if (p.hist_dq) p.hist_dq[slot] = dq;   // paper mode, recompute pass
-                if (p.td_acc && inxy_g && k >= p.gb[4] && k < p.gb[5]) {   // paper mode, forward pass: gap samples
-                    const long long lg = (((long long)(k - p.gb[4]) * p.gny + (j - p.gb[2])) * p.gnx + (i - p.gb[0])) * 3 + c;
-                    p.td_acc[lg] += (double)e * (double)e;
-                    p.gap_hist[(long long)n * p.nsamp + lg] = e;
-                }
-                emax = fmax(emax, fabs(e));
-            }
-        }
+        const T emax = c == 0 ? e_design_column<T, MP, 0>(p, tab, i, j, k0, k1, n)
+                     : c == 1 ? e_design_column<T, MP, 1>(p, tab, i, j, k0, k1, n)
+                              : e_design_column<T, MP, 2>(p, tab, i, j, k0, k1, n);
         if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
     finish_step(p.ctl, p.nblocks_d, n);

@@ -13,7 +13,7 @@ cudaError_t prepare_step();
 template <typename T>
 cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s);
 template <typename T>
-cudaError_t launch_e_design(const KParams<T>& p, int bucket, cudaStream_t s);
+cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bucket, cudaStream_t s);
 template <typename T>
 cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s);
 unsigned shell_blocks(ShellBoxes& s);   // fills s.first, returns the launch's blocks
