@@ -527,6 +527,7 @@ struct Solver : SolverBase {
         for (int m = 0; m < 2; ++m) dp[m].ctl = ctl;
         p.nblocks_s = fdtd::shell_blocks(shell);
         p.nblocks_d = c->nd ? fdtd::design_blocks(c->dn[0], c->dn[1], c->dn[2]) : 0;
+        p.nblocks_e = p.nblocks_s + p.nblocks_d;
         p.blowup = (T)1e30;
         p.n_steps = d.n_steps;
         p.tfsf_i0 = -1;
@@ -778,6 +779,31 @@ struct Solver : SolverBase {
         return e == cudaSuccess ? fdtd::launch_shell<T>(q, shell, true, c->work) : e;
     }
 
+    // One whole time step: the H phase (shell H next to the interior kernel when concurrent), then
+    // the E phase, whose shell E and design E kernels write disjoint cells and run side by side when
+    // concurrent (the last block of the two advances the step counter).
+    cudaError_t launch_one_step(const KParams<T>& q, int parity, bool concurrent, const StepMaps* mp = nullptr)
+    {
+        if (!concurrent || c->nd == 0) {
+            cudaError_t e = launch_background(q, parity, concurrent, mp);
+            return e == cudaSuccess ? fdtd::launch_e_design<T>(q, htab, bucket, c->work) : e;
+        }
+        if (!mp) mp = maps;
+        cudaError_t e = cudaEventRecord(c->fork, c->work);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+        if (e == cudaSuccess) e = fdtd::launch_shell<T>(q, shell, false, c->side);
+        if (e == cudaSuccess && fused) e = fdtd::launch_step<T>(q, mp[parity & 1], c->work);
+        if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->work, c->join, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(c->fork, c->work);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+        if (e == cudaSuccess) e = fdtd::launch_shell<T>(q, shell, true, c->side);
+        if (e == cudaSuccess) e = fdtd::launch_e_design<T>(q, htab, bucket, c->work);
+        if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->work, c->join, 0);
+        return e;
+    }
+
     // Parameters of a step with the given parity: odd steps read the second buffer of each pair.
     KParams<T> par(const KParams<T>& p, int parity) const
     {
@@ -945,8 +971,7 @@ struct Solver : SolverBase {
     {
         for (int s = n_from; s < n_to; ++s) {
             const KParams<T> q = par(p, s);
-            CK(launch_background(q, s, false, mp));
-            CK(fdtd::launch_e_design<T>(q, htab, bucket, c->work));
+            CK(launch_one_step(q, s, false, mp));
         }
         c->tim.launches += (long long)(n_to - n_from) * (fused ? 4 : 3);
     }
@@ -1146,8 +1171,7 @@ struct Solver : SolverBase {
         cudaError_t err = cudaSuccess;
         for (int s = 0; s < steps && err == cudaSuccess; ++s) {   // graphs start at even steps
             const KParams<T> q = par(p, s);
-            err = launch_background(q, s, true);
-            if (err == cudaSuccess) err = fdtd::launch_e_design<T>(q, htab, bucket, c->work);
+            err = launch_one_step(q, s, true);
         }
         if (err == cudaSuccess) err = fdtd::launch_dft<T>(dp[mode], steps, c->work);
         cudaError_t e2 = cudaStreamEndCapture(c->work, &g);

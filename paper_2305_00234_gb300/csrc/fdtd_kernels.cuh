@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_ke
                               : e_design_column<T, MP, 2>(p, tab, i, j, k0, k1, n);
         if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
-    finish_step(p.ctl, p.nblocks_d, n);
+    finish_step(p.ctl, p.nblocks_e, n);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -161,6 +161,7 @@ struct KParams {
     int ib[6];                   // interior box of the fused step kernel (empty: x0 = x1)
     unsigned nblocks_s;          // blocks of the background-E shell kernel
     unsigned nblocks_d;          // blocks of e_design_kernel
+    unsigned nblocks_e;          // blocks of the E phase (shell E + design E); the last one advances the step
     T blowup;
 };
 

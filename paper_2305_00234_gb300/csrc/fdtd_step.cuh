@@ -649,7 +649,8 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
 
 // E of the shell cells outside the design box, from H^{n+1/2} of the whole grid (after the interior
 // and shell H updates of the step); loads first within a batch, like the H kernel, with H_x, H_y of
-// the plane below a batch carried over.  Owns the step advance when there is no design box.
+// the plane below a batch carried over.  It may run concurrently with the design-E kernel: the last
+// block of the two launches advances the step.
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_e_kernel(const KParams<T> p, const ShellBoxes s)
 {
@@ -754,7 +755,7 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
         }
         if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
-    if (p.nd == 0) finish_step(p.ctl, p.nblocks_s, n);
+    finish_step(p.ctl, p.nblocks_e, n);
 }
 
 }  // namespace fdtd
