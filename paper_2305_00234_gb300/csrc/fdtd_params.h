@@ -21,7 +21,7 @@ constexpr int kMaxSnap = 16;      // steps per blocked DFT update (snapshot ring
 #define FDTD_SHELL_MINB 4
 #endif
 #ifndef FDTD_KC
-#define FDTD_KC 16
+#define FDTD_KC 8
 #endif
 #ifndef FDTD_SHELL_KZ
 #define FDTD_SHELL_KZ 8
