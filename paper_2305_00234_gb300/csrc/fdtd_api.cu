@@ -526,7 +526,8 @@ struct Solver : SolverBase {
         p.ctl = ctl;
         for (int m = 0; m < 2; ++m) dp[m].ctl = ctl;
         p.nblocks_s = fdtd::shell_blocks(shell);
-        p.nblocks_d = c->nd ? fdtd::design_blocks(c->dn[0], c->dn[1], c->dn[2]) : 0;
+        p.edz = 1;
+        p.nblocks_d = c->nd ? fdtd::design_blocks(c->dn[0], c->dn[1], c->dn[2], p.edz) : 0;
         p.nblocks_e = p.nblocks_s + p.nblocks_d;
         p.blowup = (T)1e30;
         p.n_steps = d.n_steps;

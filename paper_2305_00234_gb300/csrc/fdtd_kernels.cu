@@ -102,16 +102,22 @@ cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Columns of kShellKZ planes, shortened (by kShellPZ at a time) while the launch has fewer than
+// kMinColumnBlocks blocks, so that small grids still spread over the SMs.
 unsigned shell_blocks(ShellBoxes& s)
 {
     unsigned t = 0;
-    for (int q = 0; q < s.n; ++q) {
-        const int* B = s.b[q];
-        s.first[q] = t;
-        const unsigned wxy = (unsigned)(B[1] - B[0]) * (unsigned)(B[3] - B[2]);
-        t += (wxy + kShellCells - 1) / kShellCells * (unsigned)((B[5] - B[4] + kShellKZ - 1) / kShellKZ);
+    for (s.kz = kShellKZ;; s.kz -= kShellPZ) {
+        t = 0;
+        for (int q = 0; q < s.n; ++q) {
+            const int* B = s.b[q];
+            s.first[q] = t;
+            const unsigned wxy = (unsigned)(B[1] - B[0]) * (unsigned)(B[3] - B[2]);
+            t += (wxy + kShellCells - 1) / kShellCells * (unsigned)((B[5] - B[4] + s.kz - 1) / s.kz);
+        }
+        s.first[s.n] = t;
+        if (t >= kMinColumnBlocks || s.kz <= kShellPZ) break;
     }
-    s.first[s.n] = t;
     return t;
 }
 
@@ -133,7 +139,7 @@ cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bu
     if (p.nd == 0) return cudaSuccess;
     const dim3 b(kBX, kBY);
     const dim3 g3 = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
-    const dim3 g(g3.x, g3.y, 3 * ((g3.z + kEdZ - 1) / kEdZ));   // one block per (kEdZ planes, component)
+    const dim3 g(g3.x, g3.y, 3 * ((g3.z + p.edz - 1) / p.edz));   // one block per (p.edz planes, component)
     switch (bucket) {
     case 0: e_design_kernel<T, 0><<<g, b, 0, s>>>(p, tab); break;
     case 4: e_design_kernel<T, 4><<<g, b, 0, s>>>(p, tab); break;
@@ -152,10 +158,16 @@ cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s)
 }
 
 
-unsigned design_blocks(int dnx, int dny, int dnz)
+// Columns of kEdZ planes, halved while the launch has fewer than kMinColumnBlocks blocks.
+unsigned design_blocks(int dnx, int dny, int dnz, int& edz)
 {
     const dim3 g = grid3(dnx, dny, dnz);
-    return g.x * g.y * 3 * ((g.z + kEdZ - 1) / kEdZ);
+    unsigned t = 0;
+    for (edz = kEdZ;; edz = (edz + 1) / 2) {
+        t = g.x * g.y * 3 * ((g.z + edz - 1) / edz);
+        if (t >= kMinColumnBlocks || edz == 1) break;
+    }
+    return t;
 }
 
 template <typename T>

@@ -152,9 +152,9 @@ __device__ __forceinline__ void finish_step(int* ctl, unsigned nblocks, int n)
 
 // ---------------------------------------------------------------------------------------------
 // E update inside the working box.  A thread owns one component c of the (x, y) column of a block
-// of kEdZ planes (blockIdx.z = 3 zc + c, so the three components of a plane run in neighbouring
+// of p.edz planes (blockIdx.z = 3 zc + c, so the three components of a plane run in neighbouring
 // blocks and share its H in L2; the per-block set-up and step-advance bookkeeping are paid once per
-// kEdZ planes) and handles its planes kEdPZ at a time, every load of a batch (the pole currents
+// p.edz planes) and handles its planes kEdPZ at a time, every load of a batch (the pole currents
 // included) before any store: blended CCPR update of the design samples, background
 // update of the gap samples and of samples outside their component's sample box, point sources,
 // the E snapshot for the blocked DFT and the paper-mode records.  The working box lies outside the
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_ke
     const int zc = blockIdx.z / 3, c = blockIdx.z - 3 * zc;
     const int i = p.db[0] + blockIdx.x * kBX + threadIdx.x;
     const int j = p.db[2] + blockIdx.y * kBY + threadIdx.y;
-    const int k0 = p.db[4] + zc * kEdZ, k1 = min(p.db[5], k0 + kEdZ);
+    const int k0 = p.db[4] + zc * p.edz, k1 = min(p.db[5], k0 + p.edz);
     const int n = read_step<T>(p.ctl);
     if (i < p.db[1] && j < p.db[3]) {
         const T emax = c == 0 ? e_design_column<T, MP, 0>(p, tab, i, j, k0, k1, n)

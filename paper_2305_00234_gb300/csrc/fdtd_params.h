@@ -32,10 +32,12 @@ constexpr int kMaxSnap = 16;      // steps per blocked DFT update (snapshot ring
 #ifndef FDTD_ED_PZ
 #define FDTD_ED_PZ 1
 #endif
-constexpr int kEdZ = FDTD_ED_Z;     // z planes per thread in the design-E kernel
+constexpr int kEdZ = FDTD_ED_Z;     // most z planes per thread in the design-E kernel
 constexpr int kEdPZ = FDTD_ED_PZ;   // of which loaded per batch
 constexpr int kShellPZ = FDTD_SHELL_PZ;   // z planes per batch of loads in the shell kernels
-constexpr int kShellKZ = FDTD_SHELL_KZ;   // z planes per thread in the shell kernels (a multiple of kShellPZ)
+constexpr int kShellKZ = FDTD_SHELL_KZ;   // most z planes per thread in the shell kernels (a multiple of kShellPZ)
+// Launches smaller than this many blocks get shorter per-thread columns (more blocks) instead.
+constexpr unsigned kMinColumnBlocks = 2 * 152 * 4;
 constexpr int kKC = FDTD_KC;      // z planes per block of the fused step kernel
 
 // Fused step kernel tile: kTX x kTY cells of one z plane, kTX/2 x kTY threads, each thread two
@@ -90,6 +92,7 @@ struct ShellBoxes {
     int n;
     int b[6][6];          // half-open x0, x1, y0, y1, z0, z1
     unsigned first[7];
+    int kz;               // z planes per thread (<= kShellKZ)
 };
 
 // Tensor maps of the buffers one step reads: E^n and H^{n-1/2}, each 4-D (x, y, z, component).
@@ -161,6 +164,7 @@ struct KParams {
     int ib[6];                   // interior box of the fused step kernel (empty: x0 = x1)
     unsigned nblocks_s;          // blocks of the background-E shell kernel
     unsigned nblocks_d;          // blocks of e_design_kernel
+    int edz;                     // z planes per thread of e_design_kernel (<= kEdZ)
     unsigned nblocks_e;          // blocks of the E phase (shell E + design E); the last one advances the step
     T blowup;
 };

@@ -470,9 +470,9 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
 // ---- shell: per-cell kernels ----------------------------------------------------------------------
 // Block b -> box q; a block covers kShellCells consecutive (x, y) columns of the box (x fastest, so a
 // warp reads and writes consecutive addresses even in boxes narrower than a warp), and each thread
-// marches up to kShellKZ planes of its column in batches of kShellPZ planes whose loads are all
+// marches s.kz (at most kShellKZ) planes of its column in batches of kShellPZ planes whose loads are all
 // issued before any store.  The per-column set-up (box search, column coordinates, slab indices) is
-// paid once per kShellKZ planes; cell and psi offsets are 32-bit (a grid holds fewer than 2^31
+// paid once per s.kz planes; cell and psi offsets are 32-bit (a grid holds fewer than 2^31
 // cells) and advance by a fixed stride per plane.
 constexpr int kShellCells = kBX * kBY;
 
@@ -493,8 +493,8 @@ __device__ __forceinline__ bool shell_cell(const ShellBoxes& s, ShellCol& c)
     const unsigned yy = t / wx;
     c.x = B[0] + (int)(t - yy * wx);
     c.y = B[2] + (int)yy;
-    c.k0 = B[4] + (int)zc * kShellKZ;
-    c.k1 = min(B[5], c.k0 + kShellKZ);
+    c.k0 = B[4] + (int)zc * s.kz;
+    c.k1 = min(B[5], c.k0 + s.kz);
     return t < wxy;
 }
 
@@ -582,7 +582,9 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
     const T* __restrict__ E1 = p.E[1];
     const T* __restrict__ E2 = p.E[2];
     T exc = E0[(unsigned)cl.k0 * plane + col], eyc = E1[(unsigned)cl.k0 * plane + col];
-    for (int kb = cl.k0; kb < cl.k1; kb += P) {
+    for (int it = 0; it < kShellKZ / P; ++it) {   // compile-time trip bound; s.kz may end the column early
+        const int kb = cl.k0 + it * P;
+        if (kb >= cl.k1) break;
         HIn<T> a[P];
         T ps[P][6];
         int sz[P];
@@ -676,7 +678,7 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
             hyb = H1[(unsigned)(cl.k0 - 1) * plane + col];
         }
         T emax = T(0);
-        for (int kb = cl.k0; kb < cl.k1; kb += P) {
+        for (int kb = cl.k0; kb < cl.k1; kb += P) {   // (a compile-time trip bound here costs registers)
             T h[P][3], hm[P][4], e0[P][3], ps[P][6];
             bool on[P];
             int sz[P];
