@@ -102,8 +102,12 @@ cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Launches with fewer blocks than this (two per SM) get shorter per-thread columns, so that small
+// grids still spread over the SMs; above it long columns win (measured on 256^3 and 96x170x170).
+constexpr unsigned kMinColumnBlocks = 2 * 152;
+
 // Columns of kShellKZ planes, shortened (by kShellPZ at a time) while the launch has fewer than
-// kMinColumnBlocks blocks, so that small grids still spread over the SMs.
+// kMinColumnBlocks blocks.
 unsigned shell_blocks(ShellBoxes& s)
 {
     unsigned t = 0;

@@ -36,8 +36,6 @@ constexpr int kEdZ = FDTD_ED_Z;     // most z planes per thread in the design-E 
 constexpr int kEdPZ = FDTD_ED_PZ;   // of which loaded per batch
 constexpr int kShellPZ = FDTD_SHELL_PZ;   // z planes per batch of loads in the shell kernels
 constexpr int kShellKZ = FDTD_SHELL_KZ;   // most z planes per thread in the shell kernels (a multiple of kShellPZ)
-// Launches smaller than this many blocks get shorter per-thread columns (more blocks) instead.
-constexpr unsigned kMinColumnBlocks = 2 * 152 * 4;
 constexpr int kKC = FDTD_KC;      // z planes per block of the fused step kernel
 
 // Fused step kernel tile: kTX x kTY cells of one z plane, kTX/2 x kTY threads, each thread two
