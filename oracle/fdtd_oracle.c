@@ -36,8 +36,11 @@ typedef struct {
     cplx* c[3];
 } mat_t;
 
+typedef struct tangent_t tangent_t;
+
 struct oracle_ctx {
     oracle_grid_desc g;
+    const tangent_t* tan;     /* non-NULL while update_E advances tangent fields (oracle_tangent) */
     double* freqs;
     double* fw;
     double dt;
@@ -434,6 +437,25 @@ static double background_sample_update(const oracle_ctx* c, int comp, double e_o
     return (N * e_old + drive) / D;
 }
 
+/* Tangent-linear mode (oracle_tangent): derivative fields dE, dH, dpsi, dQ of the forward run in a
+ * density direction drho, advanced by the same discrete scheme differentiated by hand.  While
+ * update_E runs on the swapped-in tangent arrays, `tan` holds the primal E^n, E^{n+1} and Q^n. */
+struct tangent_t {
+    const double* E0[3];    /* primal E^n (copy) */
+    const double* E1[3];    /* primal E^{n+1} */
+    const cplx* Q0[3];      /* primal Q^n (copy) */
+    const double* drho;     /* direction over the design variables */
+};
+
+/* dE^{n+1} of one sample.  Background samples: the same linear update on (dE^n, d curl).  Design
+ * samples: differentiating D(rho) E^{n+1} = N(rho) E^n + drive - (2/dt) sum_p kappa_p(rho) Re{(alpha_p-1) Q_p^n}
+ *   D dE^{n+1} = N dE^n + d drive - (2/dt) sum_p kappa_p Re{(alpha_p-1) dQ_p^n}
+ *                + drho [N' E^n - (2/dt) sum_p kappa_p' Re{(alpha_p-1) Q_p^n} - D' E^{n+1}],
+ * with kappa' = -1 for m1's poles and +1 for m2's and D', N' the rho-derivatives of D, N (eps_inf, sigma
+ * with the rho(1-rho) gamma term, and sum kappa Re beta); then dQ_p <- alpha_p dQ_p + beta_p (dE^{n+1} + dE^n). */
+static double tangent_sample_update(const oracle_ctx* c, int comp, int i, int j, int k, size_t p, int cls, size_t dv,
+                                    double de_old, double ddrive);
+
 int oracle_sample_response(oracle_ctx* c, int comp, double rho, int n, const double* curl, double* e_out)
 {
     if (!c || !c->have_mat || comp < 0 || comp > 2) return 1;
@@ -488,6 +510,40 @@ static size_t gap_index(const oracle_ctx* c, int i, int j, int k)
 {
     const int* b = c->g.gap_box;
     return ((size_t)(k - b[4]) * c->gn[1] + (j - b[2])) * c->gn[0] + (i - b[0]);
+}
+
+static double tangent_sample_update(const oracle_ctx* c, int comp, int i, int j, int k, size_t p, int cls, size_t dv,
+                                    double de_old, double ddrive)
+{
+    const tangent_t* t = c->tan;
+    if (!(cls == 1 && design_sample(c, comp, i, j, k))) return background_sample_update(c, comp, de_old, ddrive);
+    const double dt = c->dt;
+    const size_t r = rho_index(c, comp, i, j, k);
+    const double rho = c->rho[r], drho = t->drho[r];
+    const int P = c->P[comp];
+    cplx* dQ = &c->Q[comp][dv * (size_t)P];              /* tangent pole currents (swapped in) */
+    const cplx* Q0 = &t->Q0[comp][dv * (size_t)P];
+    const double e0 = t->E0[comp][p], e1 = t->E1[comp][p];
+    const double kap1 = 1.0 - rho, kap2 = rho;
+    const double eps = kap1 * c->m1.eps_inf[comp] + kap2 * c->m2.eps_inf[comp];
+    const double sig = kap1 * c->m1.sigma[comp] + kap2 * c->m2.sigma[comp] + rho * (1.0 - rho) * c->gamma;
+    const double eps_r = c->m2.eps_inf[comp] - c->m1.eps_inf[comp];
+    const double sig_r = c->m2.sigma[comp] - c->m1.sigma[comp] + (1.0 - 2.0 * rho) * c->gamma;
+    double srb = 0.0, srb_r = 0.0, saq_d = 0.0, saq_r = 0.0;
+    for (int q = 0; q < P; ++q) {
+        const double kq = q < c->P1[comp] ? kap1 : kap2, kq_r = q < c->P1[comp] ? -1.0 : 1.0;
+        srb += kq * creal(c->beta[comp][q]);
+        srb_r += kq_r * creal(c->beta[comp][q]);
+        saq_d += kq * creal((c->alpha[comp][q] - 1.0) * dQ[q]);
+        saq_r += kq_r * creal((c->alpha[comp][q] - 1.0) * Q0[q]);
+    }
+    const double D = EPS0 * eps / dt + sig / 2.0 + 2.0 * srb / dt;
+    const double N = EPS0 * eps / dt - sig / 2.0 - 2.0 * srb / dt;
+    const double D_r = EPS0 * eps_r / dt + sig_r / 2.0 + 2.0 * srb_r / dt;
+    const double N_r = EPS0 * eps_r / dt - sig_r / 2.0 - 2.0 * srb_r / dt;
+    const double de_new = (N * de_old + ddrive - 2.0 * saq_d / dt + drho * (N_r * e0 - 2.0 * saq_r / dt - D_r * e1)) / D;
+    for (int q = 0; q < P; ++q) dQ[q] = c->alpha[comp][q] * dQ[q] + c->beta[comp][q] * (de_new + de_old);
+    return de_new;
 }
 
 /* H^{n+1/2} = H^{n-1/2} - (dt/mu0) curl E^n  (Eq. (Maxwells2)c), CPML-stretched derivatives. */
@@ -575,7 +631,9 @@ static void update_E(oracle_ctx* c, int n, int mode)
                     }
                     double drive = curl + point_drive(c, comp, i, j, k, n, mode, cls);
                     double* e = &c->E[comp][p];
-                    if (cls == 1 && design_sample(c, comp, i, j, k))
+                    if (c->tan)
+                        *e = tangent_sample_update(c, comp, i, j, k, p, cls, dv, *e, drive);
+                    else if (cls == 1 && design_sample(c, comp, i, j, k))
                         *e = design_sample_update(c, comp, c->rho[rho_index(c, comp, i, j, k)],
                                                   &c->Q[comp][dv * (size_t)c->P[comp]], *e, drive);
                     else
@@ -696,6 +754,95 @@ int oracle_forward(oracle_ctx* c, double* F_out, double* gap_dft_out)
     if (F_out) *F_out = F;
     c->have_fwd = 1;
     c->have_adj = 0;
+    return 0;
+}
+
+/* Swap the field, psi and pole-current arrays with the tangent ones. */
+static void swap_tangent(oracle_ctx* c, double* tE[3], double* tH[3], double* tpE[3][3], double* tpH[3][3], cplx* tQ[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        double* x = c->E[a]; c->E[a] = tE[a]; tE[a] = x;
+        x = c->H[a]; c->H[a] = tH[a]; tH[a] = x;
+        for (int b = 0; b < 3; ++b) {
+            x = c->psiE[a][b]; c->psiE[a][b] = tpE[a][b]; tpE[a][b] = x;
+            x = c->psiH[a][b]; c->psiH[a][b] = tpH[a][b]; tpH[a][b] = x;
+        }
+        cplx* q = c->Q[a]; c->Q[a] = tQ[a]; tQ[a] = q;
+    }
+}
+
+/* Forward run with its tangent-linear run in the density direction drho (n = design variables):
+ * F and dF = d/de F(rho + e drho) at e = 0, the exact derivative of the discrete objective (the
+ * forward-mode counterpart of the adjoint gradient; a check of it free of finite-difference error). */
+int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, double* dF_out)
+{
+    if (!c || !drho) return 1;
+    if (!c->have_mat) return fail(c, "materials not set");
+    if (c->nd && !c->have_rho) return fail(c, "density not set");
+    if (n != c->nvar) return fail(c, "direction has %zu values, the design has %zu", n, c->nvar);
+    const int M = c->g.n_steps;
+    double* tE[3]; double* tH[3]; double* tpE[3][3]; double* tpH[3][3]; cplx* tQ[3];
+    double* E0[3]; cplx* Q0[3];
+    for (int a = 0; a < 3; ++a) {
+        tE[a] = (double*)zalloc(c->ncell, sizeof(double));
+        tH[a] = (double*)zalloc(c->ncell, sizeof(double));
+        E0[a] = (double*)zalloc(c->ncell, sizeof(double));
+        const size_t nq = c->nd * (size_t)(c->P[a] ? c->P[a] : 1);
+        tQ[a] = (cplx*)zalloc(nq, sizeof(cplx));
+        Q0[a] = (cplx*)zalloc(nq, sizeof(cplx));
+        for (int b = 0; b < 3; ++b) {
+            tpE[a][b] = c->psiE[a][b] ? (double*)zalloc(c->ncell, sizeof(double)) : NULL;
+            tpH[a][b] = c->psiH[a][b] ? (double*)zalloc(c->ncell, sizeof(double)) : NULL;
+        }
+    }
+    cplx* tdft = (cplx*)zalloc((size_t)c->g.n_freq * 3 * c->nd, sizeof(cplx));
+    tangent_t t;
+    oracle_reset(c);
+    memset(c->dft[0], 0, (size_t)c->g.n_freq * 3 * c->nd * sizeof(cplx));
+    if (c->g.src_kind == 1) { c->inc_ready = 0; build_incident(c); }
+    for (int s = 0; s < M; ++s) {
+        update_H(c, s, 1);
+        swap_tangent(c, tE, tH, tpE, tpH, tQ);
+        update_H(c, s, 0);                               /* linear, no source */
+        swap_tangent(c, tE, tH, tpE, tpH, tQ);
+        for (int a = 0; a < 3; ++a) {
+            memcpy(E0[a], c->E[a], c->ncell * sizeof(double));
+            memcpy(Q0[a], c->Q[a], c->nd * (size_t)(c->P[a] ? c->P[a] : 1) * sizeof(cplx));
+        }
+        update_E(c, s, 1);
+        for (int a = 0; a < 3; ++a) { t.E0[a] = E0[a]; t.E1[a] = c->E[a]; t.Q0[a] = Q0[a]; }
+        t.drho = drho;
+        swap_tangent(c, tE, tH, tpE, tpH, tQ);
+        c->tan = &t;
+        update_E(c, s, 0);
+        c->tan = NULL;
+        accumulate_dft(c, tdft, s + 1);
+        swap_tangent(c, tE, tH, tpE, tpH, tQ);
+        accumulate_dft(c, c->dft[0], s + 1);
+    }
+    const int* gb = c->g.gap_box;
+    double F = 0.0, dF = 0.0;
+    for (int f = 0; f < c->g.n_freq && c->ngap; ++f)
+        for (int comp = 0; comp < 3; ++comp) {
+            const size_t o = ((size_t)f * 3 + comp) * c->nd;
+            for (int k = gb[4]; k < gb[5]; ++k)
+                for (int j = gb[2]; j < gb[3]; ++j)
+                    for (int i = gb[0]; i < gb[1]; ++i) {
+                        const size_t v = design_index(c, i, j, k);
+                        const cplx e = c->dft[0][o + v], de = tdft[o + v];
+                        F += c->fw[f] * (creal(e) * creal(e) + cimag(e) * cimag(e));
+                        dF += c->fw[f] * 2.0 * (creal(e) * creal(de) + cimag(e) * cimag(de));
+                    }
+        }
+    for (int a = 0; a < 3; ++a) {
+        free(tE[a]); free(tH[a]); free(E0[a]); free(tQ[a]); free(Q0[a]);
+        for (int b = 0; b < 3; ++b) { free(tpE[a][b]); free(tpH[a][b]); }
+    }
+    free(tdft);
+    c->have_fwd = 0;
+    c->have_adj = 0;
+    if (F_out) *F_out = F;
+    if (dF_out) *dF_out = dF;
     return 0;
 }
 
