@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -235,10 +236,15 @@ def footprint_bytes(w):
 
 
 def kernel_hash():
+    """Hash of the device-kernel sources with comments and whitespace removed (a comment edit does not
+    change the kernels the DRAM counters were taken on)."""
     h = hashlib.sha256()
     for f in ("fdtd_kernels.cuh", "fdtd_step.cuh", "fdtd_params.h"):
         with open(os.path.join(ROOT, "paper_2305_00234_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+            t = fh.read().decode()
+        t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        h.update(re.sub(r"\s+", " ", t).encode())
     return h.hexdigest()[:16]
 
 

@@ -2,21 +2,21 @@
 //
 // One Yee time step is a background step (fdtd_step.cuh: H^{n+1/2} everywhere, Eq. (Maxwells)c, and
 // E^{n+1} outside the design box, with CFS-CPML psi in the edge slabs, the TF/SF plane and point
-// sources), then
+// sources) and
 //   e_design_kernel: E^{n+1} inside the design box: the conductivity and the CCPR pole currents of
 //                    both materials weighted by 1-rho and rho (Eqs. (Maxwells)a,b, (eps_mixed),
 //                    (sigma_mixed), (Poles_mixed)), the pole recursion
 //                    Q <- Q + (alpha-1) Q + beta (E^{n+1}+E^n), and an E snapshot for the DFT;
 // and, every kMaxSnap steps, dft_kernel: the running FP64 DFT over the design box.  The gradient
-// kernel evaluates the structure of Eq. (Gradient_analytic) per voxel with a deterministic
-// warp-shuffle reduction of its squared norm.
+// kernel evaluates the structure of Eq. (Gradient_analytic) per voxel (or per E sample with the
+// per-sample density layout) with a deterministic warp-shuffle reduction of its squared norm.
 //
-// Thread layout of the per-cell kernels: block (32, 8) over (x, y); x is the fastest array axis, so
-// each warp reads and writes 128 contiguous bytes per field (FP32).
+// Thread layout of the per-cell kernels: blocks of (32, 8) threads over (x, y); x is the fastest
+// array axis, so each warp reads and writes 128 contiguous bytes per field (FP32).
 //
 // The step index n lives in device memory (ctl[0]) so that a captured CUDA graph of K steps can be
-// replayed: every kernel reads it, and the last block of e_design_kernel (of the background-E shell
-// kernel when there is no design box) advances it.
+// replayed: every kernel reads it, and the last block of the E phase (the shell-E and design-E
+// launches, counted together) advances it.
 #pragma once
 #include "fdtd_params.h"
 

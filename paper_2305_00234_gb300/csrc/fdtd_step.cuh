@@ -13,8 +13,8 @@
 //   -x/-y halo and stored; after one barrier the producer thread refills the plane's ring slots and
 //   E^{n+1} follows from the shared H and the plane below, kept in registers.  Tiles touched by the
 //   TF/SF plane, a point source or the design-box rim take a path with per-cell tests;
-// * the shell around it (walls, CPML slabs, ragged edges), updated cell by cell by shell_h_kernel
-//   (H) and then shell_e_kernel (E, after every H of the step is stored).
+// * the shell around it (walls, CPML slabs, ragged edges), updated column by column by
+//   shell_h_kernel (H) and then shell_e_kernel (E, after every H of the step is stored).
 //
 // A halo H value the interior kernel recomputes is bit-identical to the one the shell or another
 // block stores: the formula depends only on the cell and every operation is explicitly rounded.
