@@ -221,7 +221,8 @@ def workload_and_config(args):
             "100x25x100 / 6x25x6 with x and y exchanged), z-polarised plane wave along x carrying the "
             "truncated sinc x Hanning pulse at 576.5 THz, 20-cell CPML, 15 air cells of padding, "
             f"dx={'2' if args.workload[3:] in ('Al', 'Au') else '5'} nm, dt=dx/(2c0), air | Table-1 "
-            f"{args.workload[3:]}, 8 objective frequencies over 350-1000 nm, FP32 fields + FP64 DFT"),
+            f"{args.workload[3:]} with gamma=5e4, one density per E sample, 8 objective frequencies over "
+            "350-1000 nm, FP32 fields + FP64 DFT"),
         "grid": [d["nx"], d["ny"], d["nz"]], "time_steps": d["n_steps"], "design": list(dshape[::-1]),
         "pole_pairs_total": poles[0], "n_freq": len(d["freqs_hz"]), "precision": d["precision"],
         "dft_accumulators": "f64", "parallelism": f"replicas x{args.gpus}",

@@ -178,7 +178,7 @@ def sinc_hann_wave(n_steps, dt, f_c=576.5e12, rel_bw=0.5, lobes=3):
 
 
 def paper_workload(material="Au", seed=None, n_freq=8, n_steps=None, pad=15, cpml=20, design=(25, 100, 100),
-                   gap=(25, 6, 6), precision=32):
+                   gap=(25, 6, 6), precision=32, gamma=5e4, density_layout=1):
     """The paper's own optimisation setup (Sec. "Optimization setup" and "Technical details"):
     Omega_d 100 x 25 x 100 and Omega_g 6 x 25 x 6 Yee cells, z-polarised plane wave along y carrying
     the truncated-sinc pulse, 20-cell CPML, dx = 2 nm (Al, Au) or 5 nm (Si, TiO2), dt = dx / (2 c0),
@@ -186,7 +186,11 @@ def paper_workload(material="Au", seed=None, n_freq=8, n_steps=None, pad=15, cpm
     (the plane wave travels along +x through the TF/SF plane; every Table-1 material has equal x and y
     components), `pad` air cells separate the design box from the CPML (the paper gives none), and
     the time-domain energy objective is represented by n_freq frequencies evenly spaced over
-    350-1000 nm with equal weights (a uniform quadrature of its spectrum by Parseval)."""
+    350-1000 nm with equal weights (a uniform quadrature of its spectrum by Parseval).  As in the
+    paper: the damping gamma = 5e4 of Eq. (sigma_mixed) for every material, and one density per E
+    sample (density_layout 1, the N~_k count of Sec. "FDTD implementation and design export"), drawn
+    from one smooth field on the design box grown by one cell so that the three components' samples
+    of a voxel see neighbouring values."""
     idx = {"Al": 11, "Au": 12, "Si": 13, "TiO2": 14}[material]
     seed = SEED_BASE + idx if seed is None else seed
     metal = material in ("Al", "Au")
@@ -201,8 +205,15 @@ def paper_workload(material="Au", seed=None, n_freq=8, n_steps=None, pad=15, cpm
                   gap=gap, lambdas_nm=tuple(C0 / f * 1e9), src_kind=1, src_pos=(cpml + 2, 0, 0))
     dt = 0.5 * dx / C0
     d["src_wave"] = sinc_hann_wave(M, dt)
-    rho = smooth_rho(box_shape(d["design_box"]), seed + 1000, 3.0)
-    return dict(desc=d, bg=vacuum(), m1=vacuum(), m2=table_material(material), gamma=0.0, rho=rho, seed=seed)
+    d["density_layout"] = density_layout
+    nz_, ny_, nx_ = box_shape(d["design_box"])
+    if density_layout == 1:   # E_x, E_y, E_z sample sets: (z, y, x) extents grown by one off their own axis
+        field = smooth_rho((nz_ + 1, ny_ + 1, nx_ + 1), seed + 1000, 3.0)
+        rho = np.concatenate([field[:nz_ + 1, :ny_ + 1, :nx_].ravel(), field[:nz_ + 1, :ny_, :nx_ + 1].ravel(),
+                              field[:nz_, :ny_ + 1, :nx_ + 1].ravel()])
+    else:
+        rho = smooth_rho((nz_, ny_, nx_), seed + 1000, 3.0)
+    return dict(desc=d, bg=vacuum(), m1=vacuum(), m2=table_material(material), gamma=gamma, rho=rho, seed=seed)
 
 
 def box_shape(box):

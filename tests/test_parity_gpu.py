@@ -122,15 +122,16 @@ def test_step_paths(gpu, prec, nx, fused, src):
 @pytest.mark.parametrize("material", ["Si", "Au"])
 def test_paper_workload_reduced(gpu, material):
     """The paper's own setup (z-polarised plane wave carrying the truncated sinc x Hanning pulse,
-    Table-1 material in air, dt = dx/(2 c0), design box thin along the propagation axis, gap spanning
-    it) on a reduced grid with an interior box: design 24 x 32 x 32, gap 24 x 4 x 4, 8-cell CPML,
+    Table-1 material in air, dt = dx/(2 c0), gamma = 5e4, one density per E sample, design box thin
+    along the propagation axis, gap spanning it) on a reduced grid with an interior box: design 24 x 32 x 32, gap 24 x 4 x 4, 8-cell CPML,
     2400 steps, 4 objective frequencies over 350-1000 nm."""
     w = synth.paper_workload(material, design=(24, 32, 32), gap=(24, 4, 4), pad=10, cpml=8, n_steps=2400,
                              n_freq=4)
     w["desc"]["adj_tau"] = 1.0e-15
+    assert w["desc"]["density_layout"] == 1 and w["gamma"] == 5e4    # the paper's layout and damping
     g = run_gpu(gpu, w)
     assert g["p"].timings()["fused_step"] == 1
-    compare(g, run_oracle(w), 32)
+    compare(g, run_oracle(w), 32, per_voxel=False)
 
 
 @pytest.mark.parametrize("prec", [64, 32])
