@@ -70,3 +70,42 @@ def test_product_package_does_not_touch_the_oracle():
         assert "oracle" not in src, f
     for f in glob.glob(os.path.join(ROOT, "paper_2305_00234_gb300", "csrc", "*")):
         assert "oracle" not in open(f).read(), f
+
+
+def test_per_sample_layout_validation_on_host(lib):
+    """density_layout 1 grows the working box by one cell on the +x/+y/+z sides: a design box that
+    ends at the CPML is valid per voxel but not per sample; layouts other than 0 and 1 are refused."""
+    from paper_2305_00234_gb300 import _native as N
+    d = synth.base_desc(64, 64, 64, n_steps=10, cpml=8, design=(20, 20, 20), gap=(2, 2, 2))
+    d["design_box"] = [36, 56, 22, 42, 22, 42]         # x1 = 56 = nx - cpml
+    d["gap_box"] = [40, 42, 30, 32, 30, 32]
+    b0 = N.fdtd_footprint_bytes(d, [2, 2, 2])
+    with pytest.raises(N.FdtdError) as e:
+        N.fdtd_footprint_bytes(dict(d, density_layout=1), [2, 2, 2])
+    assert e.value.status == 1
+    with pytest.raises(N.FdtdError):
+        N.fdtd_footprint_bytes(dict(d, density_layout=2), [2, 2, 2])
+    d["design_box"] = [30, 50, 22, 42, 22, 42]
+    assert N.fdtd_footprint_bytes(dict(d, density_layout=1), [2, 2, 2]) > N.fdtd_footprint_bytes(d, [2, 2, 2]) > 0
+    assert b0 > 0
+
+
+@pytest.mark.parametrize("box", [[30, 50, 22, 42, 22, 42], [10, 11, 12, 20, 5, 9], [0, 0, 0, 0, 0, 0]])
+def test_binding_shapes_match_the_oracle(box):
+    """The binding's density / gradient and DFT shapes for both layouts equal the oracle's."""
+    import oracle
+    from paper_2305_00234_gb300.problem import box_shape, sample_shapes, working_box
+    import numpy as np
+    d = synth.base_desc(64, 64, 64, n_steps=4, cpml=4, precision=64)
+    d["design_box"] = box
+    for layout in (0, 1):
+        d["density_layout"] = layout
+        o = oracle.Oracle(d)
+        w = box_shape(working_box(box, layout))
+        if box_shape(box)[0] == 0:
+            assert o.vshape == (0, 0, 0)
+        else:
+            assert o.wshape == w
+            n = sum(int(np.prod(s)) for s in sample_shapes(box)) if layout else int(np.prod(box_shape(box)))
+            assert int(np.prod(o.vshape)) == n
+        o.close()
