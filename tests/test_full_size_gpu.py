@@ -106,3 +106,39 @@ def test_config2_full_size_against_the_oracle_on_the_light_cone(gpu):
     assert rel(grad[sl], ograd) <= 1e-4
     grad[sl] = 0.0
     assert not grad.any()
+
+
+def test_config2_full_size_plane_wave_against_the_oracle(gpu):
+    """The benchmark's own source at full size: the one-sided TF/SF plane at x = 14 (inside the x-wall
+    shell box) launching the plane wave along x.  The field is uniform in y and z, so the oracle runs
+    the full x extent (with the same 12-cell x CPML) on a y-z window of 101 x 101 cells, walled by PEC;
+    after N steps the window's inner 53 x 53 columns, farther than N + 1 cells from those walls, match
+    the full grid."""
+    import oracle
+    w = synth.workload("c2")
+    d = dict(w["desc"])
+    dt = d["courant"] * d["dx"] / C0
+    d.update(n_steps=N, src_fwhm_hz=2.0e15, src_t0=12 * dt, adj_tau=4 * dt, freqs_hz=[C0 / 600e-9],
+             freq_weights=[1.0])
+    w = dict(w, desc=d)
+    p = gpu.Problem(d, w["bg"], w["m1"], w["m2"], w["gamma"])
+    assert p.timings()["fused_step"] == 1
+    p.set_density(w["rho"])
+    p.forward()
+    fields = [p.field(c) for c in range(6)]
+    p.close()
+
+    n = 2 * R + 1
+    c0 = 128 - R                                        # window origin in y and z
+    dc = dict(d, ny=n, nz=n, cpml=[12, 12, 0, 0, 0, 0], design_box=[0] * 6, gap_box=[0] * 6)
+    o = oracle.Oracle(dc)
+    o.set_materials(w["bg"], w["m1"], w["m2"], w["gamma"])
+    o.forward()
+    ofields = [o.get_field(c) for c in range(6)]
+    o.close()
+    inner = slice(N + 2, n - N - 2)
+    g = np.stack([f[c0 + N + 2:c0 + n - N - 2, c0 + N + 2:c0 + n - N - 2, :] for f in fields])
+    ref = np.stack([f[inner, inner, :] for f in ofields])
+    assert np.abs(g[2]).max() > 0                       # E_z carries the wave
+    for name, s in (("E", slice(0, 3)), ("H", slice(3, 6))):
+        assert rel(g[s], ref[s]) <= 1e-4, name
