@@ -51,6 +51,9 @@ def parse(argv=None):
     ap.add_argument("--serving-slots", type=int, default=8)
     ap.add_argument("--precision-study", action="store_true",
                     help="config 3: FP32 fields + FP64 DFT vs all-FP64 build; prints one JSON line")
+    ap.add_argument("--paper-mode", action="store_true",
+                    help="time the paper's time-domain gradient (checkpoint-recompute) on the workload; "
+                         "prints one JSON line")
     return ap.parse_args(argv)
 
 
@@ -367,6 +370,46 @@ def precision_study(args):
     return 0
 
 
+def paper_mode(args):
+    """The paper's time-domain objective and history gradient (fdtd_paper_forward + fdtd_paper_gradient,
+    checkpoint-recompute) on the workload: wall time per gradient with CUDA events on the handle's
+    stream, and the same cell-update count as the main metric (forward + adjoint; the recomputed
+    forward segments are the mode's overhead)."""
+    import torch
+
+    import paper_2305_00234_gb300 as lib
+    w, cfg, ncell = workload_and_config(args)
+    if w["desc"].get("density_layout", 0) != 0:   # paper mode takes one density per voxel
+        import synth
+        w["desc"] = dict(w["desc"], density_layout=0)
+        w["rho"] = synth.smooth_rho(synth.box_shape(w["desc"]["design_box"]), w["seed"] + 1000, 3.0)
+    stream = torch.cuda.current_stream()
+    p = lib.Problem(w["desc"], w["bg"], w["m1"], w["m2"], w["gamma"], stream=stream.cuda_stream)
+    p.set_density(w["rho"])
+    grad = torch.zeros(p.dshape, dtype=torch.float32, device="cuda")
+    times = []
+    for s in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        F = p.paper_forward()
+        p.paper_gradient(grad)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    M = w["desc"]["n_steps"]
+    ms = statistics.median(times)
+    info = p.info()
+    p.close()
+    line = {"metric": "paper-mode gradient (time-domain objective, Eq. (Gradient_FDTD), checkpoint-recompute)",
+            "value": 2.0 * ncell * M / (ms * 1e-3) / 1e9, "unit": "Gcell-updates/s", "ms_per_gradient": ms,
+            "steps": args.steps, "warmup": args.warmup, "objective": F, "device_bytes": info["device_bytes"],
+            "config": cfg}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -552,6 +595,8 @@ def main(argv=None):
         return run_reference(args)
     if args.precision_study:
         return precision_study(args)
+    if args.paper_mode:
+        return paper_mode(args)
     return run_ours(args)
 
 
