@@ -51,6 +51,9 @@ def parse(argv=None):
     ap.add_argument("--serving-slots", type=int, default=8)
     ap.add_argument("--precision-study", action="store_true",
                     help="config 3: FP32 fields + FP64 DFT vs all-FP64 build; prints one JSON line")
+    ap.add_argument("--filter", action="store_true",
+                    help="time the density filter + projection and its chain rule on the workload's design box "
+                         "(R = 12 cells, beta = 52, eta = 0.5); prints one JSON line")
     ap.add_argument("--paper-mode", action="store_true",
                     help="time the paper's time-domain gradient (checkpoint-recompute) on the workload; "
                          "prints one JSON line")
@@ -370,6 +373,58 @@ def precision_study(args):
     return 0
 
 
+def filter_bench(args):
+    """fdtd_filter_project + fdtd_filter_project_grad on the design box (the paper's R = 12 cells, its
+    final beta = 52, eta = 0.5): CUDA-event time per forward + chain-rule pair.  Each call runs two
+    cone correlations (normalising sums, then the filter / its transpose); the algorithmic work is one
+    FMA per sphere tap (|d| < R) per voxel per correlation, against the FP32 FMA rate of the SMs
+    (152 SMs x 128 lanes x 2 flop x the sampled SM clock)."""
+    import numpy as np
+    import torch
+
+    import paper_2305_00234_gb300 as lib
+    import synth
+    w, cfg, ncell = workload_and_config(args)
+    shape = synth.box_shape(w["desc"]["design_box"])
+    R, beta, eta = 12.0, 52.0, 0.5
+    rho = torch.tensor(synth.smooth_rho(shape, 7, 3.0), dtype=torch.float32, device="cuda")
+    rt, rb, gin, gout = (torch.empty_like(rho) for _ in range(4))
+    gin.copy_(torch.tensor(synth.uniform_rho(shape, 8, -1.0, 1.0), dtype=torch.float32))
+    stream = torch.cuda.current_stream()
+    times = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    for s_ in range(args.warmup + args.steps):
+        if s_ == args.warmup:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lib.fdtd_filter_project(rho, rt, rb, R, beta, eta, stream.cuda_stream)
+        lib.fdtd_filter_project_grad(rt, gin, gout, R, beta, eta, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s_ >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    ms = statistics.median(times)
+    n = int(np.ceil(R)) - 1
+    d = np.arange(-n, n + 1)
+    taps = int(np.count_nonzero(np.sqrt(d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2) < R))
+    nv = int(np.prod(shape))
+    flops = 2.0 * taps * nv * 4
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    line = {"metric": "density filter + projection and chain rule (cone R = 12)", "value": ms, "unit": "ms",
+            "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "design": list(shape[::-1]),
+            "taps_per_voxel": taps,
+            "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (ms * 1e-3) / 1e12 / peak,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop (FMA) x sampled SM clock"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def paper_mode(args):
     """The paper's time-domain objective and history gradient (fdtd_paper_forward + fdtd_paper_gradient,
     checkpoint-recompute) on the workload: wall time per gradient with CUDA events on the handle's
@@ -597,6 +652,8 @@ def main(argv=None):
         return precision_study(args)
     if args.paper_mode:
         return paper_mode(args)
+    if args.filter:
+        return filter_bench(args)
     return run_ours(args)
 
 
