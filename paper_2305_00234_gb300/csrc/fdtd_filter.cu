@@ -2,12 +2,11 @@
 // projection", Eqs. (FilterFunction), (Projection), (GradientsFiltered)) on the design box.
 //
 // The cone filter is a 3-D correlation with w(d) = R - |d| over |d| < R (voxels), neighbourhoods cut at
-// the box faces.  cone_kernel computes one output voxel per thread for an 8x8x8 tile: the block stages
-// the tile plus a halo of n = ceil(R)-1 voxels of input (zero outside the box) and the (2n+1)^3 weight
-// table in shared memory, then every thread sums its sphere; the weight read is a broadcast and the
-// input reads of a warp are consecutive in x; each row runs over the sphere's taps only.  Two shared-
-// memory loads per FMA bound it (about 7100 taps per output at R = 12): 21 ms for the forward + chain
-// rule pair on a 128^3 design box, about 1% of one gradient evaluation there.
+// the box faces.  cone_kernel computes a 32x4x8 output tile per block, four x-adjacent outputs per
+// thread: the block stages the tile plus a halo of n = ceil(R)-1 voxels of input (zero outside the box)
+// and the sphere's weights, row by row, in shared memory; every thread then runs over the sphere's taps
+// with a sliding window of four inputs, so one input load and one (broadcast) weight load feed four
+// FMAs.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -22,70 +21,112 @@ void set_thread_error(const std::string& msg);
 
 namespace {
 
-constexpr int kT = 8;             // output tile edge
-constexpr int kMaxHalo = 11;      // R <= 12
-constexpr int kThreads = kT * kT * kT;
+// Output tile of one block: 32 x 4 x 8 voxels; a thread owns 4 consecutive x outputs (a warp: 8 such
+// groups x 4 rows), so each input it loads from shared memory feeds four FMAs.
+constexpr int kGX = 8, kXR = 4, kTY = 4, kTZ = 8;
+constexpr int kOX = kGX * kXR;                 // 32 outputs along x
+constexpr int kMaxHalo = 11;                   // R <= 12
+constexpr int kThreads = kGX * kTY * kTZ;      // 256
 
-// Smallest pitch >= L that is 8 mod 32: a warp reads 4 rows of 8 consecutive floats.
-__host__ __device__ inline int row_pitch(int L) { return L + ((8 - L) % 32 + 32) % 32; }
+// Smallest pitch >= L that is 1 mod 4: the 8 groups (stride 4) x 4 rows of a warp hit 32 banks.
+__host__ __device__ inline int row_pitch(int L) { return L + ((1 - L) % 4 + 4) % 4; }
 
 struct ConvArgs {
     const float* in;   // nullptr: the indicator of the box (ones inside)
     float* out;
     const float* div;  // optional: out = sum / div
     float* proj;       // optional: projection of out
-    int nx, ny, nz, n;
+    int nx, ny, nz, n, ntaps;
     float R, beta, eta, pden;
 };
+
+// Cone weight of offset (dx, dy, dz): R - |d| inside the sphere |d| < R, else 0 (not stored).
+__host__ __device__ inline float cone_weight(int dx, int dy, int dz, float R, bool& inside)
+{
+    const float d = sqrtf((float)(dx * dx + dy * dy + dz * dz));
+    inside = d < R;
+    return R - d;
+}
 
 __global__ void __launch_bounds__(kThreads) cone_kernel(const ConvArgs a)
 {
     extern __shared__ float sm[];
-    const int n = a.n, W = 2 * n + 1, L = kT + 2 * n;
-    const int P = row_pitch(L);           // x pitch of the tile; the 4 rows of a warp hit distinct banks
-    float* wt = sm;                       // W^3 weights
-    float* tile = sm + W * W * W;         // L x L x P inputs
-    int* span = (int*)(tile + L * L * P); // per (dz, dy) row: first and one-past-last nonzero weight
+    const int n = a.n, W = 2 * n + 1;
+    const int Lx = kOX + 2 * n, Ly = kTY + 2 * n, Lz = kTZ + 2 * n, P = row_pitch(Lx);
+    float* tile = sm;                                   // Lz x Ly x P inputs
+    float* wc = tile + (size_t)Lz * Ly * P;             // the sphere's weights, row by row
+    int* rows = (int*)(wc + a.ntaps);                   // per (dz, dy) row: first tap, end, offset in wc
     const int tid = threadIdx.x;
-    for (int q = tid; q < W * W * W; q += kThreads) {
-        const int dx = q % W - n, dy = (q / W) % W - n, dz = q / (W * W) - n;
-        const float d = sqrtf((float)(dx * dx + dy * dy + dz * dz));
-        wt[q] = d < a.R ? a.R - d : 0.f;
+    for (int r = tid; r < W * W; r += kThreads) {
+        int lo = W, hi = 0;
+        for (int i = 0; i < W; ++i) {
+            bool in;
+            cone_weight(i - n, r % W - n, r / W - n, a.R, in);
+            if (in) {
+                lo = min(lo, i);
+                hi = i + 1;
+            }
+        }
+        rows[3 * r] = lo;
+        rows[3 * r + 1] = hi;
     }
     __syncthreads();
-    for (int r = tid; r < W * W; r += kThreads) {   // the sphere's extent in each row (zero taps skipped)
-        int lo = W, hi = 0;
-        for (int dx = 0; dx < W; ++dx)
-            if (wt[r * W + dx] != 0.f) {
-                lo = min(lo, dx);
-                hi = dx + 1;
-            }
-        span[2 * r] = lo;
-        span[2 * r + 1] = hi;
+    if (tid == 0) {
+        int off = 0;
+        for (int r = 0; r < W * W; ++r) {
+            rows[3 * r + 2] = off;
+            off += max(0, rows[3 * r + 1] - rows[3 * r]);
+        }
     }
-    const int x0 = blockIdx.x * kT - n, y0 = blockIdx.y * kT - n, z0 = blockIdx.z * kT - n;
-    for (int q = tid; q < L * L * L; q += kThreads) {
-        const int lx = q % L, ly = (q / L) % L, lz = q / (L * L);
+    __syncthreads();
+    for (int r = tid; r < W * W; r += kThreads) {
+        bool in;
+        for (int i = rows[3 * r]; i < rows[3 * r + 1]; ++i)
+            wc[rows[3 * r + 2] + i - rows[3 * r]] = cone_weight(i - n, r % W - n, r / W - n, a.R, in);
+    }
+    const int x0 = blockIdx.x * kOX - n, y0 = blockIdx.y * kTY - n, z0 = blockIdx.z * kTZ - n;
+    for (int q = tid; q < Lx * Ly * Lz; q += kThreads) {
+        const int lx = q % Lx, ly = (q / Lx) % Ly, lz = q / (Lx * Ly);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         const bool inside = x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz;
-        tile[(lz * L + ly) * P + lx] = inside ? (a.in ? a.in[((long long)z * a.ny + y) * a.nx + x] : 1.f) : 0.f;
+        tile[(lz * Ly + ly) * P + lx] = inside ? (a.in ? a.in[((long long)z * a.ny + y) * a.nx + x] : 1.f) : 0.f;
     }
     __syncthreads();
-    const int tx = tid % kT, ty = (tid / kT) % kT, tz = tid / (kT * kT);
-    const int x = blockIdx.x * kT + tx, y = blockIdx.y * kT + ty, z = blockIdx.z * kT + tz;
-    float s = 0.f;
+    const int g = tid % kGX, ty = (tid / kGX) % kTY, tz = tid / (kGX * kTY);
+    // per output the taps are summed in the order (dz, dy, dx), one accumulator each; a sliding window
+    // of four inputs serves the thread's four x-adjacent outputs
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     for (int dz = 0; dz < W; ++dz)
         for (int dy = 0; dy < W; ++dy) {
-            const float* trow = tile + ((tz + dz) * L + (ty + dy)) * P + tx;
-            const float* wrow = wt + (dz * W + dy) * W;
-            const int lo = span[2 * (dz * W + dy)], hi = span[2 * (dz * W + dy) + 1];
-            for (int dx = lo; dx < hi; ++dx) s = fmaf(wrow[dx], trow[dx], s);
+            const int r = dz * W + dy, lo = rows[3 * r], hi = rows[3 * r + 1];
+            if (lo >= hi) continue;
+            const float* trow = tile + ((tz + dz) * Ly + (ty + dy)) * P + kXR * g;
+            const float* wr = wc + rows[3 * r + 2] - lo;
+            float v0 = trow[lo], v1 = trow[lo + 1], v2 = trow[lo + 2];
+            for (int i = lo; i < hi; ++i) {
+                const float v3 = trow[i + 3], w = wr[i];
+                s0 = fmaf(w, v0, s0);
+                s1 = fmaf(w, v1, s1);
+                s2 = fmaf(w, v2, s2);
+                s3 = fmaf(w, v3, s3);
+                v0 = v1;
+                v1 = v2;
+                v2 = v3;
+            }
         }
-    if (x >= a.nx || y >= a.ny || z >= a.nz) return;
-    const long long o = ((long long)z * a.ny + y) * a.nx + x;
-    if (a.div) s /= a.div[o];
-    a.out[o] = s;
-    if (a.proj) a.proj[o] = (tanhf(a.beta * a.eta) + tanhf(a.beta * (s - a.eta))) / a.pden;
+    const int y = blockIdx.y * kTY + ty, z = blockIdx.z * kTZ + tz;
+    if (y >= a.ny || z >= a.nz) return;
+    const float sv[kXR] = {s0, s1, s2, s3};
+#pragma unroll
+    for (int c = 0; c < kXR; ++c) {
+        const int x = blockIdx.x * kOX + kXR * g + c;
+        if (x >= a.nx) continue;
+        const long long o = ((long long)z * a.ny + y) * a.nx + x;
+        float s = sv[c];
+        if (a.div) s /= a.div[o];
+        a.out[o] = s;
+        if (a.proj) a.proj[o] = (tanhf(a.beta * a.eta) + tanhf(a.beta * (s - a.eta))) / a.pden;
+    }
 }
 
 // g = dF/drho_b * drho_b/drho_t / W  (the input of the transposed filter)
@@ -128,11 +169,20 @@ cudaError_t conv(const float* in, float* out, const float* div, float* proj, int
     a.beta = (float)beta;
     a.eta = (float)eta;
     a.pden = (float)(std::tanh(beta * eta) + std::tanh(beta * (1.0 - eta)));
-    const int W = 2 * a.n + 1, L = kT + 2 * a.n;
-    const size_t smem = sizeof(float) * (size_t)(W * W * W + L * L * row_pitch(L)) + sizeof(int) * 2 * (size_t)(W * W);
+    const int n = a.n, W = 2 * n + 1;
+    a.ntaps = 0;
+    for (int dz = -n; dz <= n; ++dz)   // the same float test as the kernel's
+        for (int dy = -n; dy <= n; ++dy)
+            for (int dx = -n; dx <= n; ++dx) {
+                bool inside;
+                cone_weight(dx, dy, dz, a.R, inside);
+                a.ntaps += inside ? 1 : 0;
+            }
+    const int Lx = kOX + 2 * n, Ly = kTY + 2 * n, Lz = kTZ + 2 * n;
+    const size_t smem = sizeof(float) * ((size_t)Lz * Ly * row_pitch(Lx) + (size_t)a.ntaps) + sizeof(int) * 3 * (size_t)(W * W);
     cudaError_t e = cudaFuncSetAttribute(cone_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const dim3 g((nx + kT - 1) / kT, (ny + kT - 1) / kT, (nz + kT - 1) / kT);
+    const dim3 g((nx + kOX - 1) / kOX, (ny + kTY - 1) / kTY, (nz + kTZ - 1) / kTZ);
     cone_kernel<<<g, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
