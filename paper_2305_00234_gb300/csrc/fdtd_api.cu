@@ -972,7 +972,7 @@ struct Solver : SolverBase {
     {
         for (int s = n_from; s < n_to; ++s) {
             const KParams<T> q = par(p, s);
-            CK(launch_one_step(q, s, false, mp));
+            CK(launch_one_step(q, s, true, mp));   // both phases on two streams, as in the captured graphs
         }
         c->tim.launches += (long long)(n_to - n_from) * (fused ? 4 : 3);
     }
