@@ -54,7 +54,8 @@ def load():
     lib.oracle_forward.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
     lib.oracle_adjoint.argtypes = [C.c_void_p]
     lib.oracle_gradient.argtypes = [C.c_void_p, P(C.c_double), C.c_size_t]
-    lib.oracle_tangent.argtypes = [C.c_void_p, P(C.c_double), C.c_size_t, P(C.c_double), P(C.c_double)]
+    lib.oracle_tangent.argtypes = [C.c_void_p, P(C.c_double), C.c_size_t, P(C.c_double), P(C.c_double),
+                                   P(C.c_double), P(C.c_double)]
     lib.oracle_paper_objective.argtypes = [C.c_void_p, P(C.c_double)]
     lib.oracle_paper_gradient.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double), C.c_size_t]
     lib.oracle_reset.argtypes = [C.c_void_p]
@@ -191,13 +192,15 @@ class Oracle:
         self._check(self.lib.oracle_gradient(self.h, _dptr(g), g.size), "gradient")
         return g
 
-    def tangent(self, drho):
+    def tangent(self, drho, time_domain=False):
         """(F, dF): the forward objective and its exact derivative along the density direction drho
-        (forward-mode differentiation of the discrete scheme; see fdtd_oracle.h)."""
+        (forward-mode differentiation of the discrete scheme; see fdtd_oracle.h); with time_domain, the
+        paper-mode energy objective and its derivative instead."""
         d = np.ascontiguousarray(drho, dtype=np.float64).ravel()
-        F, dF = C.c_double(), C.c_double()
-        self._check(self.lib.oracle_tangent(self.h, _dptr(d), d.size, C.byref(F), C.byref(dF)), "tangent")
-        return F.value, dF.value
+        F, dF, Ft, dFt = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.oracle_tangent(self.h, _dptr(d), d.size, C.byref(F), C.byref(dF), C.byref(Ft),
+                                            C.byref(dFt)), "tangent")
+        return (Ft.value, dFt.value) if time_domain else (F.value, dF.value)
 
     def paper_objective(self):
         """Time-domain objective of Eq. (Objective_analyitically_enhancement) (paper mode)."""

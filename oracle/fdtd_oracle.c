@@ -774,7 +774,8 @@ static void swap_tangent(oracle_ctx* c, double* tE[3], double* tH[3], double* tp
 /* Forward run with its tangent-linear run in the density direction drho (n = design variables):
  * F and dF = d/de F(rho + e drho) at e = 0, the exact derivative of the discrete objective (the
  * forward-mode counterpart of the adjoint gradient; a check of it free of finite-difference error). */
-int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, double* dF_out)
+int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, double* dF_out, double* Ftd_out,
+                   double* dFtd_out)
 {
     if (!c || !drho) return 1;
     if (!c->have_mat) return fail(c, "materials not set");
@@ -797,6 +798,8 @@ int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, d
     }
     cplx* tdft = (cplx*)zalloc((size_t)c->g.n_freq * 3 * c->nd, sizeof(cplx));
     tangent_t t;
+    double std_ = 0.0, dstd = 0.0;   /* time-domain gap energy sum and its tangent */
+    const int* gbx = c->g.gap_box;
     oracle_reset(c);
     memset(c->dft[0], 0, (size_t)c->g.n_freq * 3 * c->nd * sizeof(cplx));
     if (c->g.src_kind == 1) { c->inc_ready = 0; build_incident(c); }
@@ -819,6 +822,14 @@ int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, d
         accumulate_dft(c, tdft, s + 1);
         swap_tangent(c, tE, tH, tpE, tpH, tQ);
         accumulate_dft(c, c->dft[0], s + 1);
+        for (int comp = 0; comp < 3 && c->ngap; ++comp)
+            for (int k = gbx[4]; k < gbx[5]; ++k)
+                for (int j = gbx[2]; j < gbx[3]; ++j)
+                    for (int i = gbx[0]; i < gbx[1]; ++i) {
+                        const size_t p = lin(c, i, j, k);
+                        std_ += c->E[comp][p] * c->E[comp][p];
+                        dstd += 2.0 * c->E[comp][p] * tE[comp][p];
+                    }
     }
     const int* gb = c->g.gap_box;
     double F = 0.0, dF = 0.0;
@@ -843,6 +854,9 @@ int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, d
     c->have_adj = 0;
     if (F_out) *F_out = F;
     if (dF_out) *dF_out = dF;
+    const double dV = c->g.dx * c->g.dx * c->g.dx;   /* the paper-mode objective's scale */
+    if (Ftd_out) *Ftd_out = 0.5 * EPS0 * dV * c->dt * std_;
+    if (dFtd_out) *dFtd_out = 0.5 * EPS0 * dV * c->dt * dstd;
     return 0;
 }
 

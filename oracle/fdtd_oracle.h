@@ -88,8 +88,10 @@ int oracle_adjoint(oracle_ctx* c);
 int oracle_gradient(oracle_ctx* c, double* grad, size_t n);
 /* Forward run plus its tangent-linear run in the density direction drho (n = design variables):
  * F and dF = d/de F(rho + e drho) at e = 0, the exact derivative of the discrete frequency-domain
- * objective, by forward-mode differentiation of the scheme.  Invalidates the forward/adjoint state. */
-int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, double* dF_out);
+ * objective, by forward-mode differentiation of the scheme; Ftd, dFtd the same for the time-domain
+ * energy objective of paper mode.  Any output may be NULL.  Invalidates the forward/adjoint state. */
+int oracle_tangent(oracle_ctx* c, const double* drho, size_t n, double* F_out, double* dF_out, double* Ftd_out,
+                   double* dFtd_out);
 
 /* Paper mode (tiny grids): the time-domain objective of Eq. (Objective_analyitically_enhancement),
  *   F_td = (eps0/2) dx^3 dt sum_{n=1..M} sum_{gap samples} (E^n)^2   (air in the gap),
