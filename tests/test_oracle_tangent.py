@@ -101,13 +101,13 @@ def test_paper_mode_gradient_vs_tangent_linear(case):
     """Paper mode (Eq. (Gradient_FDTD) from stored histories, the time-domain energy objective of Eq.
     (Objective_analyitically_enhancement)) projected on a seeded direction, against the exact
     forward-mode derivative of the same discrete objective.  The eps_inf and sigma terms are exact
-    under either pairing of the pole term; for Lorentz pairs the pole term paired with one adjoint
-    level is exact and the printed average of two levels is close; for the Drude-Lorentz metal (a
-    real Drude pole with its static conductivity) neither pairing is exact: the single level is
-    within 1%, the printed average about 25% off."""
+    under either pairing of the pole term; the pole term paired with one adjoint level is exact once
+    the fields and pole currents have decayed by the end of the window (the derivation's assumption;
+    the metal's Drude current needs 8000 steps here, at 2000 it is 0.6% off), while the printed
+    average of two levels stays off: 2e-4 for the Lorentz dielectric, 28% for the Drude-Lorentz metal."""
     m2 = {"eps_inf": _mat(4.0, 0.0), "sigma": _mat(1.0, 2e5), "lorentz": synth.lorentz_dielectric(4, 2),
           "drude_lorentz": synth.drude_lorentz_metal(3, 2)}[case]
-    o, rho = _paper_case(m2)
+    o, rho = _paper_case(m2, steps=8000 if case == "drude_lorentz" else 2000)
     printed, single = o.paper_gradient(1)[1], o.paper_gradient(5)[1]
     drho = np.random.default_rng(3).standard_normal(rho.shape)
     Ft, dFt = o.tangent(drho, time_domain=True)
@@ -119,4 +119,4 @@ def test_paper_mode_gradient_vs_tangent_linear(case):
     elif case == "lorentz":
         assert err_s <= 1e-8 and 1e-6 < err_p < 1e-2, (err_p, err_s)
     else:
-        assert err_s < 1e-2 and 0.1 < err_p < 0.5, (err_p, err_s)
+        assert err_s <= 1e-8 and 0.2 < err_p < 0.35, (err_p, err_s)
