@@ -152,7 +152,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd
  * time-reversed functional derivative eps0 E) advances over the mirrored steps.  Readings of the
  * half-step alignment: the adjoint drive at adjoint step m is eps0 E^{M-m-1}, and the adjoint levels
  * m, m-1 stand for the paper's m+1/2, m-1/2.  pole_pairing 0 multiplies the pole term's
- * Re{Q^{M-m} - Q^{M-m+1}} by the printed average of those two levels, 1 by level m-1 alone.
+ * Re{Q^{M-m} - Q^{M-m+1}} by the printed average of those two levels, 1 by level m-1 alone.  With 1
+ * the result is the exact gradient of the discrete objective once the fields and pole currents have
+ * decayed within the window (as the derivation assumes); 0 approximates the pole term (closely for
+ * Lorentz pairs, tens of percent off for a Drude pole).
  * Extra device memory: a second state set, one state checkpoint per segment and three
  * (checkpoint_steps + 1) x 3 x design-voxel history buffers.  grad: n = design voxels, dtype 0 float32
  * / 1 float64, on_device as for fdtd_gradient.  Errors: FDTD_ERR_ARG (no design box or gap; sizes),
