@@ -23,8 +23,8 @@
  *    only.  on_device = 1 means a device pointer valid on the handle's stream (the stream passed
  *    to fdtd_create_grid; NULL = the legacy default stream); 0 means a host pointer.
  *  - Errors: every call returns a status and never throws.  fdtd_last_error() gives the text.
- *    After FDTD_ERR_CUDA or FDTD_ERR_UNSTABLE the handle accepts only fdtd_destroy,
- *    fdtd_last_error and fdtd_get_*.  A handle is not thread-safe; separate handles are.
+ *    After FDTD_ERR_CUDA, FDTD_ERR_UNSTABLE or FDTD_ERR_TIMEOUT the handle accepts only
+ *    fdtd_destroy, fdtd_last_error and fdtd_get_*.  A handle is not thread-safe; separate handles are.
  *  - Call order: create -> set_materials -> set_density -> forward -> adjoint -> gradient.
  *    set_materials/set_density invalidate earlier forward/adjoint results.
  */
@@ -45,7 +45,7 @@ typedef enum {
     FDTD_ERR_CUDA = 3,      /* CUDA runtime error (handle is dead) */
     FDTD_ERR_STATE = 4,     /* calls out of order */
     FDTD_ERR_UNSTABLE = 5,  /* non-finite or exploding field detected (handle is dead) */
-    FDTD_ERR_TIMEOUT = 6,   /* a bounded device wait gave up */
+    FDTD_ERR_TIMEOUT = 6,   /* a bounded device wait gave up (handle is dead) */
     FDTD_ERR_CANCELLED = 7  /* cancelled by fdtd_cancel */
 } fdtd_status;
 
@@ -132,6 +132,8 @@ typedef struct {
     long long fused_step;                    /* 1: the grid has an interior box for the fused TMA kernel
                                                 (x rows a multiple of 16 bytes, room inside the CPML);
                                                 0: the shell kernels cover the whole grid */
+    double interior_cells;                   /* cells of the interior box (one fused-kernel launch) */
+    double interior_design_cells;            /* of which inside the working box (no E update there) */
 } fdtd_timings;
 
 /* Create a problem on the given CUDA stream (cudaStream_t; NULL = default stream) of the current
@@ -207,18 +209,35 @@ fdtd_status fdtd_adjoint(fdtd_handle h);
 fdtd_status fdtd_gradient(fdtd_handle h, void* grad, size_t n, int dtype, int on_device);
 fdtd_status fdtd_gradient_norm(fdtd_handle h, double* grad_norm2_out);
 
-/* Parity/inspection (host buffers, synchronous).
- *  fdtd_get_field: which 0..5 = Ex,Ey,Ez,Hx,Hy,Hz after the last run, n = nx*ny*nz doubles.
+/* Parity/inspection.  dst is a host buffer (on_device 0: the call waits for the copy) or a device
+ * buffer (on_device 1: the copy is ordered on the handle's stream and the call does not wait).
+ *  fdtd_get_field: which 0..5 = Ex,Ey,Ez,Hx,Hy,Hz after the last run, n = nx*ny*nz doubles (the field
+ *    converted to FP64), (nz,ny,nx) x fastest.
  *  fdtd_get_dft: adjoint 0/1, n_doubles = 2*F*3*nd, layout (F,3,dnz,dny,dnx) complex interleaved over
  *    the working box (see density_layout).
- *  fdtd_get_index_map: which 0: (3,nz,ny,nx) per E sample: bits 0-1 voxel class (0 background,
- *    1 design, 2 gap), bit 2 PEC-fixed, bits 3/4 inside the CPML of derivative axis (c+1)%3 /
- *    (c+2)%3 at the sample's integer position, bit 5 forward dipole sample; 1: (3,nz,ny,nx) per H
- *    sample, bits 3/4 for half-integer positions; 2: per voxel design index or -1; 3: per voxel
- *    gap index or -1.  Computed on the device by the same index helpers the kernels use. */
-fdtd_status fdtd_get_field(fdtd_handle h, int which, double* dst, size_t n);
-fdtd_status fdtd_get_dft(fdtd_handle h, int adjoint, double* dst, size_t n_doubles);
+ *  fdtd_get_index_map (host only, synchronous): which 0: (3,nz,ny,nx) per E sample: bits 0-1 voxel
+ *    class (0 background, 1 design, 2 gap), bit 2 PEC-fixed, bits 3/4 inside the CPML of derivative
+ *    axis (c+1)%3 / (c+2)%3 at the sample's integer position, bit 5 forward dipole sample;
+ *    1: (3,nz,ny,nx) per H sample, bits 3/4 for half-integer positions; 2: per voxel design index
+ *    or -1; 3: per voxel gap index or -1.  Computed on the device by the same index helpers the
+ *    kernels use.
+ *  fdtd_get_gradient_constants (host, after set_materials): the per-component, per-frequency
+ *    constants of dY/drho = A + (1 - 2 rho) B (the derivative in fdtd_gradient), n_doubles = 12*F,
+ *    layout [3][F] x (A.re, A.im, B.re, B.im): the dy_drho argument of fdtd_gradient_static.
+ *  Errors: FDTD_ERR_ARG (sizes, which), FDTD_ERR_STATE (constants before set_materials). */
+fdtd_status fdtd_get_field(fdtd_handle h, int which, double* dst, size_t n, int on_device);
+fdtd_status fdtd_get_dft(fdtd_handle h, int adjoint, double* dst, size_t n_doubles, int on_device);
 fdtd_status fdtd_get_index_map(fdtd_handle h, int which, int32_t* dst, size_t n);
+fdtd_status fdtd_get_gradient_constants(fdtd_handle h, double* dst, size_t n_doubles);
+
+/* Failure-path test hook (not part of the method).  With timeout_ns > 0, every later run has block
+ * (0, 0, 0) of the interior step kernel wait at step 0, for timeout_ns, on an mbarrier that no copy
+ * completes; the wait runs out, the block records it in the handle's device flags, waits for its own
+ * copies in flight (bounded) and returns, later blocks skip their work, and the run returns
+ * FDTD_ERR_TIMEOUT; the handle is dead afterwards.  Nothing faults: the device context stays usable
+ * for other handles.  timeout_ns = 0 turns the hook off.  Errors: FDTD_ERR_ARG (a grid without an
+ * interior box, where the step kernel does not run; timeout_ns outside [0, 1e10]). */
+fdtd_status fdtd_inject_wait_timeout(fdtd_handle h, long long timeout_ns);
 
 /* Profiling: when on, runs time a sample of their kernel launches with CUDA events (see
  * fdtd_timings); fdtd_get_timings returns the sums since fdtd_reset_timings. */
@@ -243,10 +262,13 @@ fdtd_status fdtd_cancel(fdtd_handle h);
  * completion counter and the dY/drho constants) is a 1 MiB static array in device memory, which
  * every GPU that loads this library holds until the process exits.  The paper has no counterpart;
  * this is a calling convention, not part of the method.
- *  dft_fwd, dft_adj: device, (n_freq, 3, dnz, dny, dnx) complex as interleaved (re, im) doubles
- *    (the layout fdtd_get_dft returns); rho: device, design-box densities, rho_dtype 0 float32 /
- *    1 float64; design_box, gap_box (nullable): host, half-open, gap voxels get 0;
- *    dy_drho: host, [3][n_freq] x (A.re, A.im, B.re, B.im) with dY/drho = A + (1 - 2 rho) B;
+ *  It takes one density per design voxel (density_layout 0 of fdtd_grid_desc): the DFTs span
+ *    exactly the design box and the three samples of a voxel share its rho.
+ *  dft_fwd, dft_adj: device, (n_freq, 3, dnz, dny, dnx) complex as interleaved (re, im) doubles over
+ *    design_box (what fdtd_get_dft returns for a density_layout 0 handle); rho: device, design-box
+ *    densities, rho_dtype 0 float32 / 1 float64; design_box, gap_box (nullable): host, half-open,
+ *    gap voxels get 0; dy_drho: host, [3][n_freq] x (A.re, A.im, B.re, B.im) with
+ *    dY/drho = A + (1 - 2 rho) B (fdtd_get_gradient_constants of the handle that ran the DFTs);
  *    grad: device, one double per design voxel (output); grad_norm2: host, nullable (output; when
  *    given, the call waits for the stream); cuda_stream: cudaStream_t or NULL.
  *  Limits: n_freq <= 8 and at most 33,513,216 design voxels (the partial sums must fit the

@@ -22,7 +22,7 @@ EXPORTS = ("fdtd_create_grid", "fdtd_footprint_bytes", "fdtd_set_materials", "fd
            "fdtd_get_dft", "fdtd_get_index_map", "fdtd_set_profiling", "fdtd_get_timings",
            "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_filter_project", "fdtd_filter_project_grad", "fdtd_paper_forward",
-           "fdtd_paper_gradient")
+           "fdtd_paper_gradient", "fdtd_get_gradient_constants", "fdtd_inject_wait_timeout")
 
 
 class GridDesc(C.Structure):
@@ -54,7 +54,7 @@ class Timings(C.Structure):
                [(k, C.c_double) for k in ("bytes_shell_h_per_launch", "bytes_step_per_launch",
                                           "bytes_shell_e_per_launch", "bytes_ed_per_launch", "bytes_dft_per_launch",
                                           "bytes_grad_per_launch", "dft_steps_per_launch")] + \
-               [("fused_step", C.c_longlong)]
+               [("fused_step", C.c_longlong), ("interior_cells", C.c_double), ("interior_design_cells", C.c_double)]
 
 
 class FdtdError(RuntimeError):
@@ -87,8 +87,10 @@ def load_library():
         "fdtd_gradient_norm": [vp, P(d)],
         "fdtd_paper_forward": [vp, i, P(d)],
         "fdtd_paper_gradient": [vp, i, vp, sz, i, i],
-        "fdtd_get_field": [vp, i, P(d), sz],
-        "fdtd_get_dft": [vp, i, P(d), sz],
+        "fdtd_get_field": [vp, i, vp, sz, i],
+        "fdtd_get_dft": [vp, i, vp, sz, i],
+        "fdtd_get_gradient_constants": [vp, P(d), sz],
+        "fdtd_inject_wait_timeout": [vp, C.c_longlong],
         "fdtd_get_index_map": [vp, i, P(C.c_int32), sz],
         "fdtd_set_profiling": [vp, i],
         "fdtd_get_timings": [vp, P(Timings)],
@@ -250,16 +252,45 @@ def fdtd_gradient_norm(h):
     return v.value
 
 
-def fdtd_get_field(h, which, n):
-    a = np.zeros(n, dtype=np.float64)
-    _check(h, load_library().fdtd_get_field(h, which, _dptr(a), n), "fdtd_get_field")
+def _f64_out(out, n, name):
+    """(pointer, on_device, array) of an output buffer of n doubles: a new host array when out is
+    None, else a numpy float64 array or a float64 torch tensor (CUDA: on_device)."""
+    if out is None:
+        a = np.zeros(n, dtype=np.float64)
+        return a.ctypes.data, 0, a
+    if hasattr(out, "data_ptr"):
+        import torch
+        if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != n:
+            raise ValueError(f"{name}: a contiguous float64 tensor of {n} elements expected")
+        return out.data_ptr(), int(out.is_cuda), out
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous and out.size == n):
+        raise ValueError(f"{name}: a contiguous float64 array of {n} elements expected")
+    return out.ctypes.data, 0, out
+
+
+def fdtd_get_field(h, which, n, out=None):
+    """Field `which` (0..5 = Ex..Hz) as n doubles into `out` (host array or CUDA tensor; new host
+    array if None)."""
+    ptr, dev, a = _f64_out(out, n, "fdtd_get_field")
+    _check(h, load_library().fdtd_get_field(h, which, C.c_void_p(ptr), n, dev), "fdtd_get_field")
     return a
 
 
-def fdtd_get_dft(h, adjoint, n_doubles):
-    a = np.zeros(n_doubles, dtype=np.float64)
-    _check(h, load_library().fdtd_get_dft(h, int(adjoint), _dptr(a), n_doubles), "fdtd_get_dft")
+def fdtd_get_dft(h, adjoint, n_doubles, out=None):
+    ptr, dev, a = _f64_out(out, n_doubles, "fdtd_get_dft")
+    _check(h, load_library().fdtd_get_dft(h, int(adjoint), C.c_void_p(ptr), n_doubles, dev), "fdtd_get_dft")
     return a
+
+
+def fdtd_get_gradient_constants(h, n_freq):
+    """(3, n_freq, 4) doubles: A.re, A.im, B.re, B.im of dY/drho = A + (1 - 2 rho) B."""
+    a = np.zeros(12 * n_freq, dtype=np.float64)
+    _check(h, load_library().fdtd_get_gradient_constants(h, _dptr(a), a.size), "fdtd_get_gradient_constants")
+    return a.reshape(3, n_freq, 4)
+
+
+def fdtd_inject_wait_timeout(h, timeout_ns):
+    _check(h, load_library().fdtd_inject_wait_timeout(h, int(timeout_ns)), "fdtd_inject_wait_timeout")
 
 
 def fdtd_get_index_map(h, which, n):
@@ -299,27 +330,45 @@ def fdtd_last_error(h):
     return m.decode() if m else ""
 
 
-def fdtd_gradient_static(dft_fwd, dft_adj, rho, design_box, gap_box, n_freq, dy_drho, grad, stream=None):
+def fdtd_gradient_static(dft_fwd, dft_adj, rho, design_box, gap_box, n_freq, dy_drho, grad, stream=None,
+                         norm=True):
     """No-allocation gradient from caller-owned device buffers (torch CUDA tensors): dft_fwd,
-    dft_adj float64 (interleaved complex), rho float32/float64, grad float64 (written).  dy_drho:
-    host array (3, n_freq, 4).  Returns the squared norm of the gradient."""
+    dft_adj float64 (interleaved complex, (n_freq, 3, dnz, dny, dnx) over design_box), rho
+    float32/float64 (one per design voxel), grad float64 (one per design voxel, written).  dy_drho:
+    host array (3, n_freq, 4).  Returns the squared norm of the gradient (the call then waits for
+    the stream), or None with norm=False (the call only enqueues work on the stream).
+
+    Every buffer size is checked here against design_box and n_freq, before the call: an undersized
+    buffer would make the kernel read or write past its end."""
     import torch
-    for t in (dft_fwd, dft_adj, grad):
+    for name, t in (("dft_fwd", dft_fwd), ("dft_adj", dft_adj), ("grad", grad)):
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-            raise TypeError("dft_fwd, dft_adj and grad must be contiguous float64 CUDA tensors")
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
     if not (rho.is_cuda and rho.is_contiguous() and rho.dtype in (torch.float32, torch.float64)):
         raise TypeError("rho must be a contiguous float32/float64 CUDA tensor")
-    db = (C.c_int * 6)(*[int(x) for x in design_box])
+    db_l = [int(x) for x in design_box]
+    if len(db_l) != 6 or any(db_l[2 * a + 1] <= db_l[2 * a] for a in range(3)):
+        raise ValueError("design_box must be 6 ints with a non-empty extent on every axis")
+    nd = (db_l[1] - db_l[0]) * (db_l[3] - db_l[2]) * (db_l[5] - db_l[4])
+    nf = int(n_freq)
+    if dft_fwd.numel() != 6 * nf * nd or dft_adj.numel() != 6 * nf * nd:
+        raise ValueError(f"dft_fwd and dft_adj must hold 2*3*n_freq*nd = {6 * nf * nd} doubles")
+    if rho.numel() < nd or grad.numel() < nd:
+        raise ValueError(f"rho and grad must hold at least nd = {nd} values")
+    cst = np.ascontiguousarray(dy_drho, dtype=np.float64)
+    if cst.shape != (3, nf, 4):
+        raise ValueError(f"dy_drho must have shape (3, n_freq, 4) = (3, {nf}, 4)")
+    db = (C.c_int * 6)(*db_l)
     gb = (C.c_int * 6)(*[int(x) for x in gap_box]) if gap_box is not None else None
-    cst = np.ascontiguousarray(dy_drho, dtype=np.float64).ravel()
+    cst = cst.ravel()
     norm2 = C.c_double()
     rc = load_library().fdtd_gradient_static(C.c_void_p(dft_fwd.data_ptr()), C.c_void_p(dft_adj.data_ptr()),
                                              C.c_void_p(rho.data_ptr()), 0 if rho.dtype == torch.float32 else 1,
-                                             db, gb, int(n_freq), _dptr(cst), C.c_void_p(grad.data_ptr()),
-                                             C.byref(norm2), C.c_void_p(stream or 0))
+                                             db, gb, nf, _dptr(cst), C.c_void_p(grad.data_ptr()),
+                                             C.byref(norm2) if norm else None, C.c_void_p(stream or 0))
     if rc != FDTD_OK:
         raise FdtdError(rc, load_library().fdtd_last_error(None).decode())
-    return norm2.value
+    return norm2.value if norm else None
 
 
 def _f32_dev(t, name):

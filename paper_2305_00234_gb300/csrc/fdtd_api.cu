@@ -684,7 +684,8 @@ struct Solver : SolverBase {
         base.hg = (T)(0.5 * gamma);
         CK(cudaMemcpyAsync(poles, &tab, sizeof tab, cudaMemcpyHostToDevice, c->work));
         htab = tab;
-        CK(cudaMemcpyAsync(AB, ab.data(), ab.size() * sizeof(double2), cudaMemcpyHostToDevice, c->work));
+        ab_host = ab;
+        CK(cudaMemcpyAsync(AB, ab_host.data(), ab_host.size() * sizeof(double2), cudaMemcpyHostToDevice, c->work));
         build_incident(bg);
         refresh_params();
     }
@@ -984,7 +985,7 @@ struct Solver : SolverBase {
         CK(cudaStreamSynchronize(c->work));
         if (h[2] & 4) {
             c->dead = true;
-            throw Err{FDTD_ERR_CUDA, "a TMA plane of the step kernel did not arrive within its time limit"};
+            throw Err{FDTD_ERR_TIMEOUT, "a wait of the step kernel gave up after its time limit"};
         }
         if (h[2] & 1) {
             c->dead = true;
@@ -1269,7 +1270,7 @@ struct Solver : SolverBase {
         CK(cudaStreamSynchronize(c->work));
         if (hctl[2] & 4) {
             c->dead = true;
-            throw Err{FDTD_ERR_CUDA, "a TMA plane of the step kernel did not arrive within its time limit"};
+            throw Err{FDTD_ERR_TIMEOUT, "a wait of the step kernel gave up after its time limit"};
         }
         if (hctl[2] & 1) {
             c->dead = true;
@@ -1481,20 +1482,44 @@ struct Solver : SolverBase {
         return v;
     }
 
-    void get_field(int which, double* dst)
+    // Field / DFT copies: to a host buffer (synchronous) or, on_device, to a device buffer on the
+    // handle's stream (ordered after the last run, no host wait).
+    void get_field(int which, double* dst, int on_device)
     {
         T* src = cur_field(which);
+        if (on_device) {
+            CK(fdtd::launch_to_double<T>(src, (long long)c->ncell, dst, c->work));
+            c->tim.launches++;
+            return;
+        }
         std::vector<T> h(c->ncell);
         CK(cudaMemcpyAsync(h.data(), src, c->ncell * sizeof(T), cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
         for (size_t q = 0; q < c->ncell; ++q) dst[q] = (double)h[q];
     }
 
-    void get_dft(int adjoint, double* dst)
+    void get_dft(int adjoint, double* dst, int on_device)
     {
-        CK(cudaMemcpyAsync(dst, dft[adjoint ? 1 : 0], c->nd * 3 * c->d.n_freq * sizeof(double2), cudaMemcpyDeviceToHost,
-                           c->work));
-        CK(cudaStreamSynchronize(c->work));
+        CK(cudaMemcpyAsync(dst, dft[adjoint ? 1 : 0], c->nd * 3 * c->d.n_freq * sizeof(double2),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->work));
+        if (!on_device) CK(cudaStreamSynchronize(c->work));
+    }
+
+    // Failure-path test hook: with timeout_ns > 0, block (0, 0, 0) of the interior kernel at step 0
+    // of every later run waits, with that limit, on an mbarrier that no copy completes (0: off).
+    void set_stall(long long timeout_ns)
+    {
+        base.stall_ns = timeout_ns;
+        refresh_params();
+    }
+
+    // dY/drho constants of the last set_materials: [3][n_freq] x (A.re, A.im, B.re, B.im).
+    void gradient_constants(double* dst) const
+    {
+        for (size_t q = 0; q < ab_host.size(); ++q) {
+            dst[2 * q] = ab_host[q].x;
+            dst[2 * q + 1] = ab_host[q].y;
+        }
     }
 
     void index_map(int which, int32_t* dst, size_t n)
@@ -1782,18 +1807,54 @@ fdtd_status fdtd_gradient_norm(fdtd_handle h, double* out)
     return guarded(h, [&] { dispatch(h, [&](auto* s) { *out = s->grad_norm2(); }); });
 }
 
-fdtd_status fdtd_get_field(fdtd_handle h, int which, double* dst, size_t n)
+fdtd_status fdtd_get_field(fdtd_handle h, int which, double* dst, size_t n, int on_device)
 {
     if (fdtd_status s = check_handle(h, true)) return s;
     if (!h->impl || which < 0 || which > 5 || n != h->ncell || !dst) return FDTD_ERR_ARG;
-    return guarded(h, [&] { dispatch(h, [&](auto* s) { s->get_field(which, dst); }); });
+    return guarded(h, [&] {
+        if (on_device) enter(h);
+        dispatch(h, [&](auto* s) { s->get_field(which, dst, on_device); });
+        if (on_device) leave(h);
+    });
 }
 
-fdtd_status fdtd_get_dft(fdtd_handle h, int adjoint, double* dst, size_t n_doubles)
+fdtd_status fdtd_get_dft(fdtd_handle h, int adjoint, double* dst, size_t n_doubles, int on_device)
 {
     if (fdtd_status s = check_handle(h, true)) return s;
     if (!h->impl || !dst || n_doubles != 2 * h->nd * 3 * (size_t)h->d.n_freq) return FDTD_ERR_ARG;
-    return guarded(h, [&] { dispatch(h, [&](auto* s) { s->get_dft(adjoint, dst); }); });
+    return guarded(h, [&] {
+        if (on_device) enter(h);
+        dispatch(h, [&](auto* s) { s->get_dft(adjoint, dst, on_device); });
+        if (on_device) leave(h);
+    });
+}
+
+fdtd_status fdtd_get_gradient_constants(fdtd_handle h, double* dst, size_t n_doubles)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    if (!h->impl || !h->has_mat) {
+        h->err = "set_materials first";
+        return FDTD_ERR_STATE;
+    }
+    if (!dst || n_doubles != 3 * 4 * (size_t)h->d.n_freq) {
+        h->err = "gradient constants: expected 12 * n_freq doubles";
+        return FDTD_ERR_ARG;
+    }
+    return guarded(h, [&] { dispatch(h, [&](auto* s) { s->gradient_constants(dst); }); });
+}
+
+fdtd_status fdtd_inject_wait_timeout(fdtd_handle h, long long timeout_ns)
+{
+    if (fdtd_status s = check_handle(h)) return s;
+    if (!h->impl || !h->impl->has_interior()) {
+        h->err = "the wait-timeout hook needs a grid with an interior box (fused step kernel)";
+        return FDTD_ERR_ARG;
+    }
+    if (timeout_ns < 0 || timeout_ns > 10LL * 1000 * 1000 * 1000) {
+        h->err = "timeout_ns must lie in [0, 1e10]";
+        return FDTD_ERR_ARG;
+    }
+    return guarded(h, [&] { dispatch(h, [&](auto* s) { s->set_stall(timeout_ns); }); });
 }
 
 fdtd_status fdtd_get_index_map(fdtd_handle h, int which, int32_t* dst, size_t n)
@@ -1834,6 +1895,8 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
             ndi *= std::max(0, std::min(ib[2 * a + 1], db[2 * a + 1]) - std::max(ib[2 * a], db[2 * a]));
         if (box_count(db) == 0) ndi = 0.0;
         bst = 12.0 * ts * ni - 3.0 * ts * ndi;
+        t.interior_cells = ni;
+        t.interior_design_cells = ndi;
         bsh = 9.0 * ts * (nc - ni);
         bse = 9.0 * ts * ((nc - ni) - (nd - ndi));
     }

@@ -165,6 +165,8 @@ struct KParams {
     int edz;                     // z planes per thread of e_design_kernel (<= kEdZ)
     unsigned nblocks_e;          // blocks of the E phase (shell E + design E); the last one advances the step
     T blowup;
+    long long stall_ns;          // failure-path test hook (step_kernel): > 0 makes block (0, 0, 0) at step 0 wait
+                                 // this long on an mbarrier that nothing completes; 0 = off
 };
 
 template <typename T>

@@ -138,14 +138,14 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 constexpr unsigned long long kWaitNs = 50ull * 1000 * 1000;   // a TMA plane arrives in microseconds
 
-// Wait for the phase of the given parity; false after kWaitNs (or 2^26 tries) without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+// Wait for the phase of the given parity; false after limit_ns (or 2^26 tries) without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (int t = 0; t < (1 << 26); ++t) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
     constexpr int NE = StepCfg<T>::NE, NH = StepCfg<T>::NH;
     constexpr int PN = kSYH * kHW;    // one component of a new-H tile
     using S = StepSmem<T>;
+    static_assert((NE + NH + 1) * sizeof(uint64_t) <= S::bars, "mbarriers of the rings and the test hook");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     T* sE = (T*)sm;                                                    // NE slots of S::e_slot bytes
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
         tma_load_4d(hslot(r % NH), &m.h, bar + NE + r % NH, i0 - kOX, j0 - 1, k_first + r, 0);
     };
     if (tid == 0) {
-        for (int s = 0; s < NE + NH; ++s) mbar_init(bar + s, 1);
+        for (int s = 0; s < NE + NH + 1; ++s) mbar_init(bar + s, 1);   // [NE + NH]: the test hook's barrier
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_shared();
     }
@@ -394,6 +395,9 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
         const int es1 = es + 1 == NE ? 0 : es + 1;
         bool ok = true;
         if (r == 0) ok = mbar_wait(bar, 0);
+        // failure-path test hook: a wait on a barrier that no copy completes runs out after stall_ns
+        if (r == 0 && p.stall_ns > 0 && n == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+            ok = mbar_wait(bar + NE + NH, 0, (unsigned long long)p.stall_ns) && ok;
         ok = ok && mbar_wait(bar + es1, ((r + 1) / NE) & 1);
         ok = ok && mbar_wait(bar + NE + hs, (r / NH) & 1);
         const int pa = path[r];

@@ -24,12 +24,19 @@ class FdtdGrad(torch.autograd.Function):
         problem.set_density(rho.detach().contiguous())
         F, _ = problem.forward()
         ctx.problem = problem
+        ctx.version = problem.version       # the handle's density and forward DFT this node depends on
         ctx.rho_meta = (rho.shape, rho.dtype, rho.device)
         return torch.tensor(F, dtype=torch.float64, device=rho.device)
 
     @staticmethod
     def backward(ctx, grad_F):
         p = ctx.problem
+        if p.version != ctx.version:
+            # the handle keeps one density and one forward DFT: a later forward on the same Problem
+            # replaced the state this node's adjoint run needs
+            raise RuntimeError("FdtdGrad.backward: the Problem ran another forward (or set another density) "
+                               "after this one; run backward before the next forward on the same Problem, "
+                               "or use one Problem per graph node")
         shape, dtype, device = ctx.rho_meta
         p.adjoint()
         g = torch.empty(shape, dtype=dtype if dtype in (torch.float32, torch.float64) else torch.float32,

@@ -59,6 +59,8 @@ class Problem:
         self.nvar = int(np.prod(self.dshape))
         self.ngap = int(np.prod(self.gshape))
         self.poles_total = [len(m1["poles"][k]) + len(m2["poles"][k]) for k in range(3)]
+        # bumped by every call that replaces the density or the forward result the handle holds
+        self.version = 0
 
     def close(self):
         if getattr(self, "h", None):
@@ -78,9 +80,11 @@ class Problem:
         self.close()
 
     def set_density(self, rho):
+        self.version += 1
         N.fdtd_set_density(self.h, rho)
 
     def forward(self):
+        self.version += 1
         ng = 2 * self.nf * 3 * self.ngap
         F, g = N.fdtd_forward(self.h, ng)
         return F, (g[0::2] + 1j * g[1::2]).reshape((self.nf, 3) + self.gshape)
@@ -108,12 +112,27 @@ class Problem:
     def gradient_norm2(self):
         return N.fdtd_gradient_norm(self.h)
 
-    def field(self, which):
-        return N.fdtd_get_field(self.h, which, int(np.prod(self.n))).reshape(self.n)
+    def field(self, which, out=None):
+        """Field `which` (0..5 = Ex..Hz) as FP64 (nz, ny, nx); `out`: a float64 CUDA tensor of that
+        many elements receives it on the device (ordered on the handle's stream)."""
+        a = N.fdtd_get_field(self.h, which, int(np.prod(self.n)), out)
+        return a.reshape(self.n) if out is None else out
 
-    def dft(self, adjoint=False):
-        a = N.fdtd_get_dft(self.h, adjoint, 2 * self.nf * 3 * self.nd)
+    def dft(self, adjoint=False, out=None):
+        """DFT over the working box, complex (F, 3, dnz, dny, dnx); `out`: a float64 CUDA tensor of
+        2 F 3 nd elements receives the interleaved (re, im) values on the device instead."""
+        a = N.fdtd_get_dft(self.h, adjoint, 2 * self.nf * 3 * self.nd, out)
+        if out is not None:
+            return out
         return (a[0::2] + 1j * a[1::2]).reshape((self.nf, 3) + self.wshape)
+
+    def gradient_constants(self):
+        """(3, F, 4): A.re, A.im, B.re, B.im of dY/drho = A + (1 - 2 rho) B (fdtd_gradient_static's dy_drho)."""
+        return N.fdtd_get_gradient_constants(self.h, self.nf)
+
+    def inject_wait_timeout(self, timeout_ns):
+        """Failure-path test hook (fdtd_inject_wait_timeout)."""
+        N.fdtd_inject_wait_timeout(self.h, timeout_ns)
 
     def index_map(self, which):
         shape = ((3,) + self.n) if which <= 1 else self.n

@@ -80,3 +80,22 @@ def test_autograd_fp32_gradient_dtype(lib):
     assert np.allclose(rho.grad.cpu().numpy(), 2.0 * g2, rtol=1e-5, atol=1e-6 * np.abs(g2).max())
     p.close()
     p2.close()
+
+
+def test_backward_after_another_forward_on_the_same_problem_is_refused(lib):
+    """A Problem holds one density and one forward DFT: a second forward before the first node's
+    backward would silently give both nodes the gradient at the second density, so it raises."""
+    import torch
+    w = synth.scaled_workload("c4", 32, 200)
+    p = lib.Problem(w["desc"], w["bg"], w["m1"], w["m2"], w["gamma"])
+    r1 = torch.tensor(w["rho"], dtype=torch.float32, device="cuda", requires_grad=True)
+    r2 = torch.tensor(0.5 * w["rho"], dtype=torch.float32, device="cuda", requires_grad=True)
+    F1 = lib.objective(r1, p)
+    F2 = lib.objective(r2, p)
+    with pytest.raises(RuntimeError, match="another forward"):
+        (F1 + F2).backward()
+    # one node at a time works
+    F1 = lib.objective(r1, p)
+    F1.backward()
+    assert torch.isfinite(r1.grad).all()
+    p.close()
