@@ -297,6 +297,48 @@ fdtd_status fdtd_filter_project(const float* rho, float* rho_t, float* rho_b, in
 fdtd_status fdtd_filter_project_grad(const float* rho_t, const float* dF_drho_b, float* dF_drho, int nx, int ny,
                                      int nz, double R, double beta, double eta, void* cuda_stream);
 
+/* Batches: several runs (forward or adjoint runs of different handles, different grid sizes) advanced
+ * together by one persistent kernel, for serving many gradient evaluations at once.  The paper has no
+ * counterpart; the arithmetic of a batched run is the method's (the same cell updates, pole recursion and
+ * DFT as fdtd_forward / fdtd_adjoint; the background cells take the per-cell kernels' rounding instead
+ * of the fused interior kernel's, so results agree with fdtd_forward to FP32 rounding, and a run's results
+ * do not depend on which other runs share its launches).
+ *  Each launch is one CUDA graph (zero the work counter, the persistent kernel) whose kernel takes work
+ *  items (one phase, H or E, of one step of one run, on 4-8 z planes x 256-1024 (x, y) columns) from a global
+ *  counter in an order where every item only waits for items numbered before it; every wait is bounded.
+ *  fdtd_batch_create: on the current device; work is ordered after cuda_stream (NULL: legacy default
+ *    stream) at each fdtd_batch_run and the stream waits for it afterwards.
+ *  fdtd_batch_submit: adjoint 0 starts the handle's forward run (after set_materials and set_density),
+ *    adjoint 1 its adjoint run (after a forward run, batched or not; the drive is built as in
+ *    fdtd_adjoint).  At most 16 runs at a time; FP32 handles on the batch's device only.  Until the run
+ *    ends, calls on the handle other than fdtd_get_*, fdtd_last_error and fdtd_destroy (which removes
+ *    the run) return FDTD_ERR_STATE.
+ *  fdtd_batch_run: one launch advancing every submitted run by up to max_steps steps; returns the
+ *    handles whose runs ended in done[0 .. *n_done) with their status (FDTD_OK, or FDTD_ERR_UNSTABLE /
+ *    FDTD_ERR_CUDA for that handle alone); capacity must be at least the number of runs in the batch.
+ *    A finished forward run leaves the handle as fdtd_forward does (fdtd_get_objective gives F and the
+ *    gap DFT); a finished adjoint run as fdtd_adjoint does (fdtd_gradient next).  If a wait of the
+ *    persistent kernel gives up: FDTD_ERR_TIMEOUT, and the batch and its handles are dead.
+ *  fdtd_batch_set_wait_limit: the limit of one wait (default 1 s); gate = 1 is a failure-path test hook
+ *    that makes the first work item also wait on a flag nothing sets, so that the next fdtd_batch_run
+ *    returns FDTD_ERR_TIMEOUT without any GPU fault.
+ *  fdtd_batch_info: runs in the batch and launches made.
+ *  Errors: FDTD_ERR_ARG, FDTD_ERR_STATE (call order, full batch, dead batch), FDTD_ERR_OOM,
+ *  FDTD_ERR_TIMEOUT, FDTD_ERR_CUDA; the text of batch calls is in fdtd_last_error(NULL). */
+typedef struct fdtd_batch_ctx* fdtd_batch;
+fdtd_status fdtd_batch_create(void* cuda_stream, fdtd_batch* out);
+fdtd_status fdtd_batch_submit(fdtd_batch b, fdtd_handle h, int adjoint);
+fdtd_status fdtd_batch_run(fdtd_batch b, int max_steps, fdtd_handle* done, fdtd_status* done_status, int capacity,
+                           int* n_done);
+fdtd_status fdtd_batch_set_wait_limit(fdtd_batch b, long long wait_ns, int gate);
+fdtd_status fdtd_batch_info(fdtd_batch b, int* n_runs, long long* launches);
+fdtd_status fdtd_batch_destroy(fdtd_batch b);
+
+/* Objective of the handle's last forward run (fdtd_forward or a batched forward run): F_out (host,
+ * nullable) and the gap DFT (host, nullable, as fdtd_forward's gap_dft_out).  FDTD_ERR_STATE before a
+ * forward run. */
+fdtd_status fdtd_get_objective(fdtd_handle h, double* F_out, double* gap_dft_out);
+
 /* Message of the handle's last failed call; with h = NULL, of the calling thread's last failed
  * call (fdtd_create_grid and fdtd_footprint_bytes have no handle to report through). */
 const char* fdtd_last_error(fdtd_handle h);

@@ -11,7 +11,7 @@ from ._native import (FdtdError, fdtd_adjoint, fdtd_cancel, fdtd_create_grid, fd
                       fdtd_get_index_map, fdtd_get_info, fdtd_get_timings, fdtd_gradient,
                       fdtd_gradient_norm, fdtd_last_error, fdtd_reset_timings, fdtd_set_density,
                       fdtd_set_materials, fdtd_set_profiling, load_library)
-from .problem import Problem, box_shape, problem  # noqa: F401
+from .problem import Batch, Problem, box_shape, problem  # noqa: F401
 
 
 def __getattr__(name):

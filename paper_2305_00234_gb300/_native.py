@@ -22,7 +22,9 @@ EXPORTS = ("fdtd_create_grid", "fdtd_footprint_bytes", "fdtd_set_materials", "fd
            "fdtd_get_dft", "fdtd_get_index_map", "fdtd_set_profiling", "fdtd_get_timings",
            "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_filter_project", "fdtd_filter_project_grad", "fdtd_paper_forward",
-           "fdtd_paper_gradient", "fdtd_get_gradient_constants", "fdtd_inject_wait_timeout")
+           "fdtd_paper_gradient", "fdtd_get_gradient_constants", "fdtd_inject_wait_timeout", "fdtd_batch_create",
+           "fdtd_batch_submit", "fdtd_batch_run", "fdtd_batch_set_wait_limit", "fdtd_batch_info", "fdtd_batch_destroy",
+           "fdtd_get_objective")
 
 
 class GridDesc(C.Structure):
@@ -90,6 +92,13 @@ def load_library():
         "fdtd_get_field": [vp, i, vp, sz, i],
         "fdtd_get_dft": [vp, i, vp, sz, i],
         "fdtd_get_gradient_constants": [vp, P(d), sz],
+        "fdtd_batch_create": [vp, P(vp)],
+        "fdtd_batch_submit": [vp, vp, i],
+        "fdtd_batch_run": [vp, i, P(vp), P(C.c_int), i, P(C.c_int)],
+        "fdtd_batch_set_wait_limit": [vp, C.c_longlong, i],
+        "fdtd_batch_info": [vp, P(C.c_int), P(C.c_longlong)],
+        "fdtd_batch_destroy": [vp],
+        "fdtd_get_objective": [vp, P(d), P(d)],
         "fdtd_inject_wait_timeout": [vp, C.c_longlong],
         "fdtd_get_index_map": [vp, i, P(C.c_int32), sz],
         "fdtd_set_profiling": [vp, i],
@@ -369,6 +378,61 @@ def fdtd_gradient_static(dft_fwd, dft_adj, rho, design_box, gap_box, n_freq, dy_
     if rc != FDTD_OK:
         raise FdtdError(rc, load_library().fdtd_last_error(None).decode())
     return norm2.value if norm else None
+
+
+MAX_BATCH = 16
+
+
+def _check_batch(rc, what):
+    if rc != FDTD_OK:
+        msg = load_library().fdtd_last_error(None)
+        raise FdtdError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+
+def fdtd_batch_create(stream=None):
+    b = C.c_void_p()
+    _check_batch(load_library().fdtd_batch_create(C.c_void_p(stream or 0), C.byref(b)), "fdtd_batch_create")
+    return b
+
+
+def fdtd_batch_submit(b, h, adjoint=False):
+    lib = load_library()
+    rc = lib.fdtd_batch_submit(b, h, int(bool(adjoint)))
+    if rc != FDTD_OK:
+        msg = (lib.fdtd_last_error(h) if h else b"") or lib.fdtd_last_error(None)
+        raise FdtdError(rc, "fdtd_batch_submit: " + (msg.decode() if msg else ""))
+
+
+def fdtd_batch_run(b, max_steps):
+    """One persistent launch; returns [(handle value, status), ...] of the runs that ended."""
+    done = (C.c_void_p * MAX_BATCH)()
+    st = (C.c_int * MAX_BATCH)()
+    n = C.c_int()
+    _check_batch(load_library().fdtd_batch_run(b, int(max_steps), done, st, MAX_BATCH, C.byref(n)), "fdtd_batch_run")
+    return [(done[q], st[q]) for q in range(n.value)]
+
+
+def fdtd_batch_set_wait_limit(b, wait_ns, gate=False):
+    _check_batch(load_library().fdtd_batch_set_wait_limit(b, int(wait_ns), int(bool(gate))), "fdtd_batch_set_wait_limit")
+
+
+def fdtd_batch_info(b):
+    n, l = C.c_int(), C.c_longlong()
+    _check_batch(load_library().fdtd_batch_info(b, C.byref(n), C.byref(l)), "fdtd_batch_info")
+    return {"runs": n.value, "launches": l.value}
+
+
+def fdtd_batch_destroy(b):
+    if b:
+        load_library().fdtd_batch_destroy(b)
+
+
+def fdtd_get_objective(h, n_gap_doubles=0):
+    F = C.c_double()
+    g = np.zeros(max(n_gap_doubles, 1), dtype=np.float64)
+    _check(h, load_library().fdtd_get_objective(h, C.byref(F), _dptr(g) if n_gap_doubles else None),
+           "fdtd_get_objective")
+    return F.value, g[:n_gap_doubles]
 
 
 def _f32_dev(t, name):

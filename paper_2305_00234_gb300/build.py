@@ -1,6 +1,6 @@
 """Build the sm_103a CUDA library ``libfdtdccpr.so`` in-tree (next to this file).
 
-Two translation units (host C-ABI, kernels) compile in parallel with one -gencode; the shared
+The translation units (host C-ABI, kernels, batch kernel, no-allocation entry, filter) compile in parallel with one -gencode; the shared
 library links the CUDA runtime statically so it needs nothing but the driver at run time.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libfdtdccpr.so")
-SOURCES = ["fdtd_api.cu", "fdtd_kernels.cu", "fdtd_noalloc.cu", "fdtd_filter.cu"]
+SOURCES = ["fdtd_api.cu", "fdtd_kernels.cu", "fdtd_batch.cu", "fdtd_noalloc.cu", "fdtd_filter.cu"]
 HEADERS = ["fdtd_kernels.cuh", "fdtd_step.cuh", "fdtd_launch.h", "fdtd_params.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

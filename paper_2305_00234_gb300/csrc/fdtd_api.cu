@@ -98,6 +98,16 @@ Material import_material(const fdtd_ccpr_material* m, const char* what)
     return out;
 }
 
+// Work-item shape of a batched run: z planes sz and (x, y) columns cw per item.  Small grids take small
+// items (more of them in flight, fewer planes marched by each thread), large grids large ones (less
+// per-item overhead).
+void batch_shape(const fdtd_grid_desc& d, int* sz, int* cw)
+{
+    const long long nxy = (long long)d.nx * d.ny;
+    *sz = nxy * d.nz >= (1LL << 21) ? 2 * fdtd::kMinBatchSZ : fdtd::kMinBatchSZ;
+    *cw = nxy >= 32768 ? 4 * fdtd::kBatchThreads : fdtd::kBatchThreads;
+}
+
 // CFS-CPML coefficients at position u (cells) along an axis of n cells with lo/hi layers.
 void pml_point(const fdtd_grid_desc& d, double dt, int lo, int hi, int n, double u, double* kinv, double* b, double* c)
 {
@@ -321,6 +331,10 @@ struct fdtd_ctx {
     int dbu[6] = {0, 0, 0, 0, 0, 0};   // the caller's design box
     int dn[3] = {0, 0, 0}, gn[3] = {0, 0, 0};
     bool has_mat = false, has_rho = false, has_fwd = false, has_adj = false, has_grad = false, dead = false;
+    double F_last = 0.0;                // objective of the last forward run
+    struct fdtd_batch_ctx* batch = nullptr;   // the batch running one of this handle's runs, if any
+    int batch_slot = -1;
+    cudaEvent_t bfence = nullptr;       // orders the handle's stream before the batch's
     std::string err;
     std::atomic<int> cancel{0};
     size_t bytes = 0;
@@ -1282,6 +1296,12 @@ struct Solver : SolverBase {
     double forward(double* gap_out)
     {
         run(0);
+        return forward_epilogue(gap_out);
+    }
+
+    // After a forward run: the gap DFT to the host and the objective F = sum_f w_f sum_gap |Ehat|^2.
+    double forward_epilogue(double* gap_out)
+    {
         const fdtd_grid_desc& d = c->d;
         const size_t ns = c->ngap * 3 * d.n_freq;
         gap_dft.assign(2 * ns, 0.0);
@@ -1307,6 +1327,13 @@ struct Solver : SolverBase {
     // Adjoint drive: 2F basis pulses b_q(t) = g(t) {cos, sin}(w_f (t - t0a)) and, per gap sample,
     // the real coefficients r_g with sum_q r_{g,q} Bhat_q(w_f) = w_f conj(Ehat_g(w_f)).
     void adjoint()
+    {
+        adjoint_drive();
+        run(1);
+    }
+
+    // Build and upload the adjoint drive from the forward gap DFT (the part of the adjoint before its run).
+    void adjoint_drive()
     {
         const fdtd_grid_desc& d = c->d;
         const int F = d.n_freq, nb = 2 * F, M = d.n_steps;
@@ -1410,7 +1437,35 @@ struct Solver : SolverBase {
             std::memcpy(pa.sb, base.gb, sizeof pa.sb);
             refresh_params();
         }
-        run(1);
+    }
+
+    // ---- batched runs (fdtd_batch_*) --------------------------------------------------------------
+    // Start a run of the given mode inside a batch: zero the state (on the handle's stream) and describe
+    // the run for the persistent kernel; the adjoint mode first builds its drive, as fdtd_adjoint does.
+    void batch_prepare(int mode, fdtd::BatchSlot<T>* slot)
+    {
+        if (mode == 1) adjoint_drive();
+        reset_state(mode);
+        const KParams<T>& p = mode ? pa : pf;
+        slot->kp[0] = par(p, 0);
+        slot->kp[1] = par(p, 1);
+        slot->dp = dp[mode];
+        batch_shape(c->d, &slot->sz, &slot->cw);
+        slot->nslab = (c->d.nz + slot->sz - 1) / slot->sz;
+        slot->nxyc = (int)(((long long)c->d.nx * c->d.ny + slot->cw - 1) / slot->cw);
+        slot->n0 = 0;
+    }
+
+    // Flags of a finished batched run (the device flags the kernels raise): throws like run().
+    void batch_check()
+    {
+        int hctl[4];
+        CK(cudaMemcpyAsync(hctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        if (hctl[2] & 1) {
+            c->dead = true;
+            throw Err{FDTD_ERR_UNSTABLE, "non-finite or exploding field during the run"};
+        }
     }
 
     void gradient(void* out, int dtype, int on_device)
@@ -1603,12 +1658,388 @@ fdtd_status check_handle(fdtd_handle h, bool allow_dead = false)
 {
     if (!h) return FDTD_ERR_ARG;
     if (h->dead && !allow_dead) return FDTD_ERR_STATE;
+    if (h->batch && !allow_dead) {   // a run of this handle is in a batch: only inspection until it ends
+        h->err = "a run of this handle is in progress in a batch";
+        return FDTD_ERR_STATE;
+    }
     return FDTD_OK;
 }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------------
+// Batches: several runs advanced together by one persistent kernel (fdtd_batch.cu)
+// ---------------------------------------------------------------------------------------------
+struct fdtd_batch_ctx {
+    int device = 0;
+    cudaStream_t user = nullptr, stream = nullptr;
+    cudaEvent_t fence = nullptr;
+    fdtd::BatchSlot<float>* slots = nullptr;    // [kMaxBatch] on the device
+    unsigned* prog = nullptr;                   // [kMaxBatch][kMaxBatchSlabs]
+    unsigned long long* ticket = nullptr;
+    int* err = nullptr;                         // [2]
+    int* gate = nullptr;                        // test hook flag, stays 0
+    bool use_gate = false;
+    unsigned long long wait_ns = 1000000000ull; // one second
+    struct Run {
+        fdtd_ctx* h = nullptr;
+        int mode = 0, done = 0, M = 0;
+    };
+    Run runs[fdtd::kMaxBatch];
+    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};       // per pole bucket 4 / 8 / 16 (kept: the
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};   // kernel node is updated through it)
+    cudaGraphNode_t knode[3] = {nullptr, nullptr, nullptr};
+    unsigned blocks[3] = {0, 0, 0};
+    long long launches = 0;
+    bool dead = false;
+    std::string err_msg;
+    std::vector<void*> allocs;
+    std::mutex mu;                               // fdtd_destroy of a member handle may come from any thread
+};
+
+namespace {
+
+int bucket_index(int bucket) { return bucket <= 4 ? 0 : (bucket <= 8 ? 1 : 2); }
+
+void batch_detach(fdtd_ctx* h)
+{
+    fdtd_batch_ctx* b = h->batch;
+    if (!b) return;
+    std::lock_guard<std::mutex> lock(b->mu);
+    cudaStreamSynchronize(b->stream);           // no launch of the batch may still touch the handle
+    if (h->batch_slot >= 0) b->runs[h->batch_slot] = fdtd_batch_ctx::Run{};
+    h->batch = nullptr;
+    h->batch_slot = -1;
+}
+
+// The launch's graph for one pole bucket: zero the ticket counter and the error words, then the kernel.
+// Captured once; every launch only rewrites the kernel's parameter block.
+void batch_graph(fdtd_batch_ctx* b, int bi, const fdtd::BatchLaunch& L)
+{
+    const void* fn = fdtd::batch_kernel_fn<float>(bi == 0 ? 4 : (bi == 1 ? 8 : 16));
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)fn;
+    kp.gridDim = dim3(b->blocks[bi]);
+    kp.blockDim = dim3(fdtd::kBatchThreads);
+    kp.sharedMemBytes = 0;
+    void* args[1] = {(void*)&L};
+    kp.kernelParams = args;
+    if (!b->exec[bi]) {
+        cudaGraph_t g = nullptr;
+        CK(cudaGraphCreate(&g, 0));
+        cudaGraphNode_t m1 = nullptr, m2 = nullptr, k = nullptr;
+        cudaMemsetParams ms{};
+        ms.dst = b->ticket;
+        ms.value = 0;
+        ms.elementSize = 4;
+        ms.width = 2;                         // one unsigned long long
+        ms.height = 1;
+        cudaError_t e = cudaGraphAddMemsetNode(&m1, g, nullptr, 0, &ms);
+        ms.dst = b->err;
+        if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&m2, g, &m1, 1, &ms);
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&k, g, &m2, 1, &kp);
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            CK(e);
+        }
+        b->graph[bi] = g;
+        b->exec[bi] = ex;
+        b->knode[bi] = k;
+    } else {
+        CK(cudaGraphExecKernelNodeSetParams(b->exec[bi], b->knode[bi], &kp));
+    }
+}
+
+}  // namespace
+
 extern "C" {
+
+fdtd_status fdtd_batch_create(void* cuda_stream, fdtd_batch* out)
+{
+    if (!out) return FDTD_ERR_ARG;
+    *out = nullptr;
+    fdtd_batch_ctx* b = new (std::nothrow) fdtd_batch_ctx();
+    if (!b) return FDTD_ERR_OOM;
+    fdtd_status st = guarded(nullptr, [&] {
+        CK(cudaGetDevice(&b->device));
+        b->user = (cudaStream_t)cuda_stream;
+        CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&b->fence, cudaEventDisableTiming));
+        auto alloc = [&](size_t n) {
+            void* p = nullptr;
+            if (cudaMallocFromPoolAsync(&p, n, device_pool(b->device), b->stream) != cudaSuccess) {
+                cudaGetLastError();
+                throw Err{FDTD_ERR_OOM, "batch: device allocation failed"};
+            }
+            b->allocs.push_back(p);
+            return p;
+        };
+        b->slots = (fdtd::BatchSlot<float>*)alloc(sizeof(fdtd::BatchSlot<float>) * fdtd::kMaxBatch);
+        b->prog = (unsigned*)alloc(sizeof(unsigned) * fdtd::kMaxBatch * fdtd::kMaxBatchSlabs);
+        b->ticket = (unsigned long long*)alloc(256);
+        b->err = (int*)alloc(256);
+        b->gate = (int*)alloc(256);
+        CK(cudaMemsetAsync(b->err, 0, 256, b->stream));
+        CK(cudaMemsetAsync(b->gate, 0, 256, b->stream));
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+        for (int bi = 0; bi < 3; ++bi) {
+            int per = 0;
+            CK(fdtd::batch_blocks_per_sm<float>(bi == 0 ? 4 : (bi == 1 ? 8 : 16), &per));
+            b->blocks[bi] = (unsigned)std::max(1, sms * std::max(1, per));
+        }
+        CK(cudaStreamSynchronize(b->stream));
+    });
+    if (st != FDTD_OK) {
+        fdtd_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_batch_submit(fdtd_batch b, fdtd_handle h, int adjoint)
+{
+    if (!b || (adjoint != 0 && adjoint != 1)) return FDTD_ERR_ARG;
+    if (b->dead) {
+        g_last_error = "batch is dead after a failed launch";
+        return FDTD_ERR_STATE;
+    }
+    if (fdtd_status s = check_handle(h)) return s;
+    if (h->device != b->device || h->d.precision != 32) {
+        h->err = "batch: the handle must be an FP32 handle on the batch's device";
+        return FDTD_ERR_ARG;
+    }
+    if (adjoint ? !h->has_fwd : (!h->has_mat || (h->nd && !h->has_rho))) {
+        h->err = adjoint ? "batched adjoint before forward" : "set_materials and set_density first";
+        return FDTD_ERR_STATE;
+    }
+    int bsz = 0, bcw = 0;
+    batch_shape(h->d, &bsz, &bcw);
+    const long long nslab = (h->d.nz + bsz - 1) / bsz;
+    const long long nxyc = ((long long)h->d.nx * h->d.ny + bcw - 1) / bcw;
+    if (2LL * h->d.n_steps * nxyc >= (1LL << 32) || nslab > fdtd::kMaxBatchSlabs) {
+        h->err = "batch: grid or step count too large for the batch's work-item counters";
+        return FDTD_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(b->mu);
+    int slot = -1;
+    for (int q = 0; q < fdtd::kMaxBatch; ++q)
+        if (!b->runs[q].h) {
+            slot = q;
+            break;
+        }
+    if (slot < 0) {
+        h->err = "batch: all " + std::to_string(fdtd::kMaxBatch) + " slots are in use";
+        return FDTD_ERR_STATE;
+    }
+    h->cancel.store(0);
+    return guarded(h, [&] {
+        enter(h);
+        fdtd::BatchSlot<float> hs{};
+        as<float>(h)->batch_prepare(adjoint, &hs);
+        hs.prog = b->prog + (size_t)slot * fdtd::kMaxBatchSlabs;
+        CK(cudaMemsetAsync(hs.prog, 0, sizeof(unsigned) * hs.nslab, h->work));
+        CK(cudaMemcpyAsync(b->slots + slot, &hs, sizeof hs, cudaMemcpyHostToDevice, h->work));
+        CK(cudaEventRecord(h->bfence, h->work));
+        CK(cudaStreamWaitEvent(b->stream, h->bfence, 0));
+        CK(cudaStreamSynchronize(h->work));     // the slot description above lives on this stack
+        if (adjoint)
+            h->has_adj = h->has_grad = false;
+        else
+            h->has_fwd = h->has_adj = h->has_grad = false;
+        b->runs[slot] = fdtd_batch_ctx::Run{h, adjoint, 0, h->d.n_steps};
+        h->batch = b;
+        h->batch_slot = slot;
+    });
+}
+
+fdtd_status fdtd_batch_run(fdtd_batch b, int max_steps, fdtd_handle* done, fdtd_status* done_status, int capacity,
+                           int* n_done)
+{
+    if (!b || max_steps < 1 || !n_done || capacity < 0 || (capacity > 0 && (!done || !done_status))) return FDTD_ERR_ARG;
+    *n_done = 0;
+    if (b->dead) {
+        g_last_error = "batch is dead after a failed launch";
+        return FDTD_ERR_STATE;
+    }
+    std::lock_guard<std::mutex> lock(b->mu);
+    struct Act {
+        int slot, nph, cnt;
+        long long items;
+        int bucket;
+    };
+    std::vector<Act> act;
+    for (int q = 0; q < fdtd::kMaxBatch; ++q) {
+        const auto& r = b->runs[q];
+        if (!r.h) continue;
+        const int cnt = std::min(max_steps, r.M - r.done);
+        int bsz = 0, bcw = 0;
+        batch_shape(r.h->d, &bsz, &bcw);
+        const long long nslab = (r.h->d.nz + bsz - 1) / bsz;
+        const long long nxyc = ((long long)r.h->d.nx * r.h->d.ny + bcw - 1) / bcw;
+        act.push_back(Act{q, 2 * cnt, cnt, nslab * nxyc, as<float>(r.h)->bucket});
+    }
+    if (act.empty()) return FDTD_OK;
+    if ((int)act.size() > capacity) {   // every run may finish in this launch
+        g_last_error = "batch: capacity below the number of runs in the batch";
+        return FDTD_ERR_ARG;
+    }
+    std::stable_sort(act.begin(), act.end(), [](const Act& a, const Act& c) { return a.nph > c.nph; });
+    fdtd::BatchLaunch L{};
+    L.nruns = (int)act.size();
+    L.pre[0] = 0;
+    int bucket = 4;
+    for (int j = 0; j < L.nruns; ++j) {
+        L.slot[j] = act[j].slot;
+        L.pre[j + 1] = L.pre[j] + act[j].items;
+        bucket = std::max(bucket, act[j].bucket);
+    }
+    // segments of rounds with the same number of taking-part runs (a prefix of the sorted list)
+    int g = 0, nseg = 0;
+    long long t0 = 0;
+    for (int m = L.nruns; m > 0; --m) {
+        const int g1 = act[m - 1].nph;       // runs 0 .. m-1 take part in rounds [g, g1)
+        if (g1 <= g) continue;
+        L.seg_g0[nseg] = g;
+        L.seg_m[nseg] = m;
+        L.seg_t0[nseg] = t0;
+        t0 += (long long)(g1 - g) * L.pre[m];
+        g = g1;
+        ++nseg;
+    }
+    L.nseg = nseg;
+    L.seg_g0[nseg] = g;
+    L.seg_t0[nseg] = t0;
+    L.slots = b->slots;
+    L.ticket = b->ticket;
+    L.err = b->err;
+    L.gate = b->use_gate ? b->gate : nullptr;
+    L.wait_ns = b->wait_ns;
+    return guarded(nullptr, [&] {
+        CK(cudaSetDevice(b->device));
+        CK(cudaEventRecord(b->fence, b->user));
+        CK(cudaStreamWaitEvent(b->stream, b->fence, 0));
+        std::vector<int> n0(act.size());
+        for (size_t j = 0; j < act.size(); ++j) {
+            n0[j] = b->runs[act[j].slot].done;
+            CK(cudaMemcpyAsync(&b->slots[act[j].slot].n0, &n0[j], sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        }
+        const int bi = bucket_index(bucket);
+        batch_graph(b, bi, L);
+        CK(cudaGraphLaunch(b->exec[bi], b->stream));
+        b->launches++;
+        int herr[2] = {0, 0};
+        CK(cudaMemcpyAsync(herr, b->err, sizeof herr, cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        if (herr[0]) {
+            b->dead = true;
+            for (auto& r : b->runs)
+                if (r.h) {
+                    r.h->dead = true;
+                    r.h->err = "batch: a dependency wait of the persistent kernel gave up after its time limit";
+                    r.h->batch = nullptr;
+                    r.h->batch_slot = -1;
+                    r = fdtd_batch_ctx::Run{};
+                }
+            throw Err{FDTD_ERR_TIMEOUT, "batch: a dependency wait of the persistent kernel gave up after its time limit "
+                                        "(work item " + std::to_string(herr[1]) + ")"};
+        }
+        for (const Act& a : act) {
+            auto& r = b->runs[a.slot];
+            r.done += a.cnt;
+            if (r.done < r.M) continue;
+            fdtd_ctx* h = r.h;
+            const int mode = r.mode;
+            r = fdtd_batch_ctx::Run{};
+            h->batch = nullptr;
+            h->batch_slot = -1;
+            h->tim.launches += 1;
+            const fdtd_status st = guarded(h, [&] {
+                CK(cudaEventRecord(b->fence, b->stream));
+                CK(cudaStreamWaitEvent(h->work, b->fence, 0));
+                Solver<float>* s = as<float>(h);
+                s->batch_check();
+                if (mode == 0) {
+                    h->F_last = s->forward_epilogue(nullptr);
+                    h->has_fwd = true;
+                } else {
+                    h->has_adj = true;
+                }
+                leave(h);
+            });
+            done[*n_done] = h;
+            done_status[*n_done] = st;
+            ++*n_done;
+        }
+        CK(cudaEventRecord(b->fence, b->stream));
+        CK(cudaStreamWaitEvent(b->user, b->fence, 0));
+    });
+}
+
+fdtd_status fdtd_batch_set_wait_limit(fdtd_batch b, long long wait_ns, int gate)
+{
+    if (!b || wait_ns <= 0 || wait_ns > 60LL * 1000 * 1000 * 1000 || (gate != 0 && gate != 1)) return FDTD_ERR_ARG;
+    std::lock_guard<std::mutex> lock(b->mu);
+    b->wait_ns = (unsigned long long)wait_ns;
+    b->use_gate = gate != 0;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_batch_info(fdtd_batch b, int* n_runs, long long* launches)
+{
+    if (!b) return FDTD_ERR_ARG;
+    std::lock_guard<std::mutex> lock(b->mu);
+    int n = 0;
+    for (const auto& r : b->runs) n += r.h ? 1 : 0;
+    if (n_runs) *n_runs = n;
+    if (launches) *launches = b->launches;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_batch_destroy(fdtd_batch b)
+{
+    if (!b) return FDTD_ERR_ARG;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    {
+        std::lock_guard<std::mutex> lock(b->mu);
+        for (auto& r : b->runs)
+            if (r.h) {
+                r.h->batch = nullptr;
+                r.h->batch_slot = -1;
+                r = fdtd_batch_ctx::Run{};
+            }
+    }
+    for (auto& e : b->exec)
+        if (e) cudaGraphExecDestroy(e);
+    for (auto& g : b->graph)
+        if (g) cudaGraphDestroy(g);
+    if (b->stream) {
+        for (void* p : b->allocs) cudaFreeAsync(p, b->stream);
+        cudaStreamSynchronize(b->stream);
+        cudaStreamDestroy(b->stream);
+    }
+    if (b->fence) cudaEventDestroy(b->fence);
+    delete b;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_get_objective(fdtd_handle h, double* F_out, double* gap_dft_out)
+{
+    if (fdtd_status s = check_handle(h, true)) return s;
+    if (!h->has_fwd) {
+        h->err = "no forward result";
+        return FDTD_ERR_STATE;
+    }
+    return guarded(h, [&] {
+        if (F_out) *F_out = h->F_last;
+        if (gap_dft_out)
+            dispatch(h, [&](auto* s) { std::memcpy(gap_dft_out, s->gap_dft.data(), s->gap_dft.size() * sizeof(double)); });
+    });
+}
 
 fdtd_status fdtd_footprint_bytes(const fdtd_grid_desc* desc, const int p_total[3], size_t* bytes)
 {
@@ -1647,6 +2078,7 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* desc, void* cuda_stream, fdtd
         CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->bfence, cudaEventDisableTiming));
         c->dt = desc->courant * desc->dx / kC0;
         c->ncell = (size_t)desc->nx * desc->ny * desc->nz;
         c->nd = (size_t)box_count(c->d.design_box);
@@ -1730,6 +2162,7 @@ fdtd_status fdtd_forward(fdtd_handle h, double* F_out, double* gap_dft_out)
         dispatch(h, [&](auto* s) { F = s->forward(gap_dft_out); });
         leave(h);
         if (F_out) *F_out = F;
+        h->F_last = F;
         h->has_fwd = true;
         h->has_adj = h->has_grad = false;
     });
@@ -1959,6 +2392,7 @@ const char* fdtd_last_error(fdtd_handle h) { return h ? h->err.c_str() : g_last_
 fdtd_status fdtd_destroy(fdtd_handle h)
 {
     if (!h) return FDTD_ERR_ARG;
+    batch_detach(h);
     cudaSetDevice(h->device);
     if (h->work) cudaStreamSynchronize(h->work);
     h->impl.reset();
@@ -1968,6 +2402,7 @@ fdtd_status fdtd_destroy(fdtd_handle h)
     }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->fence) cudaEventDestroy(h->fence);
+    if (h->bfence) cudaEventDestroy(h->bfence);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     if (h->side) cudaStreamDestroy(h->side);

@@ -54,6 +54,25 @@ __device__ __forceinline__ T stretch(T d, const T* __restrict__ tab, int s, T* p
 template <typename T>
 __device__ __forceinline__ T ldg_t(const T* p) { return __ldg(p); }
 
+// Load of solver state (fields, psi, pole currents, density, snapshots, DFT accumulators).  CG: through
+// L2 only, bypassing L1, for work items of a persistent kernel, where an earlier item on the same SM may
+// have left lines in L1 that another SM has since rewritten.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldf(const T* p)
+{
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+template <bool CG, typename T>
+__device__ __forceinline__ cpx<T> ldf(const cpx<T>* p)
+{
+    using V = typename vec2_of<T>::type;
+    const V v = ldf<CG>(reinterpret_cast<const V*>(p));
+    return cpx<T>{v.x, v.y};
+}
+
 template <typename T>
 __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p)
 {
@@ -72,14 +91,14 @@ __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p)
 // constant-bank operands).
 // dq (paper mode): sum_p dkappa_p/drho Re{Q_p^{n+1} - Q_p^n} of this sample (-1 for m1's poles,
 // +1 for m2's), the pole term of Eq. (Gradient_FDTD).
-template <typename T, int MP, int C>
+template <typename T, int MP, int C, bool CG = false>
 __device__ __forceinline__ void design_load(const KParams<T>& p, long long dv, cpx<T> (&q)[MP > 0 ? MP : 1])
 {
     const int P = p.P[C];
     const cpx<T>* __restrict__ Q = p.Q[C];
 #pragma unroll
     for (int pp = 0; pp < MP; ++pp)
-        if (pp < P) q[pp] = Q[pp * p.nd + dv];
+        if (pp < P) q[pp] = ldf<CG>(Q + pp * p.nd + dv);
 }
 
 template <typename T, int MP, int C>
@@ -170,7 +189,7 @@ constexpr int ed_min_blocks()
 }
 
 // One component C of the (x, y) column (i, j), planes [k0, k1); returns max |E| of its samples.
-template <typename T, int MP, int C>
+template <typename T, int MP, int C, bool CG = false>
 __device__ __forceinline__ T e_design_column(const KParams<T>& p, const PoleTable<T>& tab, int i, int j, int k0, int k1, int n)
 {
     constexpr int PZ = kEdPZ;
@@ -202,14 +221,14 @@ __device__ __forceinline__ T e_design_column(const KParams<T>& p, const PoleTabl
             const unsigned id = (unsigned)k * plane + col;
             const long long dv = (long long)(k - p.db[4]) * p.dplane + dcol;
             const int la = C == 0 ? j : (C == 1 ? k : i), lb = C == 0 ? k : (C == 1 ? i : j);
-            ha[r] = Ha[id];
-            hb[r] = Hb[id];
-            ham[r] = la > 0 ? Ha[id - oa] : T(0);
-            hbm[r] = lb > 0 ? Hb[id - ob] : T(0);
-            e0[r] = Ec[id];
+            ha[r] = ldf<CG>(Ha + id);
+            hb[r] = ldf<CG>(Hb + id);
+            ham[r] = la > 0 ? ldf<CG>(Ha + id - oa) : T(0);
+            hbm[r] = lb > 0 ? ldf<CG>(Hb + id - ob) : T(0);
+            e0[r] = ldf<CG>(Ec + id);
             ds[r] = inxy_m && k >= p.mb[C][4] && k < p.mb[C][5] && !(inxy_g && k >= p.gb[4] && k < p.gb[5]);
-            rho[r] = ds[r] ? rc[dv] : T(0);
-            if (ds[r]) design_load<T, MP, C>(p, dv, q[r]);
+            rho[r] = ds[r] ? ldf<CG>(rc + dv) : T(0);
+            if (ds[r]) design_load<T, MP, C, CG>(p, dv, q[r]);
         }
 #pragma unroll
         for (int r = 0; r < PZ; ++r) {
@@ -261,20 +280,18 @@ __global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_ke
 // block sums sum_s E^{n0+s+1} (cos, -sin)(w_f (n0+s+1) dt) in the accumulation type A, and adds
 // them to the FP64 accumulators, which are read and written once per block instead of every step.
 // ---------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kReduceThreads) dft_kernel(const DParams<T> d, int cnt)
+// The fold of one voxel v: steps n0 .. n0 + cnt - 1 (cnt <= kMaxSnap).
+template <typename T, bool CG>
+__device__ __forceinline__ void dft_voxel(const DParams<T>& d, long long v, int n0, int cnt)
 {
-    const long long v = (long long)blockIdx.x * kReduceThreads + threadIdx.x;
-    if (v >= d.nd) return;
-    const int n0 = __ldcg(d.ctl) - cnt;
     T e[kMaxSnap][3];
 #pragma unroll
     for (int s = 0; s < kMaxSnap; ++s) {
         if (s < cnt) {
             const T* sp = d.snap + (long long)((n0 + s) % d.K) * 3 * d.nd + v;
-            e[s][0] = sp[0];
-            e[s][1] = sp[d.nd];
-            e[s][2] = sp[2 * d.nd];
+            e[s][0] = ldf<CG>(sp);
+            e[s][1] = ldf<CG>(sp + d.nd);
+            e[s][2] = ldf<CG>(sp + 2 * d.nd);
         }
     }
     for (int f = 0; f < d.nf; ++f) {
@@ -293,12 +310,20 @@ __global__ void __launch_bounds__(kReduceThreads) dft_kernel(const DParams<T> d,
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double2* acc = d.dft + (long long)(f * 3 + c) * d.nd + v;
-            double2 a = *acc;
+            double2 a = ldf<CG>(acc);
             a.x += (double)re[c];
             a.y += (double)im[c];
             *acc = a;
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) dft_kernel(const DParams<T> d, int cnt)
+{
+    const long long v = (long long)blockIdx.x * kReduceThreads + threadIdx.x;
+    if (v >= d.nd) return;
+    dft_voxel<T, false>(d, v, __ldcg(d.ctl) - cnt, cnt);
 }
 
 // ---------------------------------------------------------------------------------------------

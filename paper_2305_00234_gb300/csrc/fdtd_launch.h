@@ -39,5 +39,10 @@ template <typename T>
 cudaError_t launch_paper_grad(const PParams<T>& g, cudaStream_t s);
 template <typename T>
 cudaError_t launch_index_map(const KParams<T>& p, int which, int32_t* out, cudaStream_t s);
+// persistent batch kernel (fdtd_batch.cu): its function for a pole bucket, and resident blocks per SM
+template <typename T>
+const void* batch_kernel_fn(int bucket);
+template <typename T>
+cudaError_t batch_blocks_per_sm(int bucket, int* out);
 
 }  // namespace fdtd

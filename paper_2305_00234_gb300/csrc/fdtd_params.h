@@ -212,6 +212,45 @@ struct GParams {
     unsigned* counter;
 };
 
+// ---- batched runs: one persistent launch advances several runs (different grids) together ----------
+#ifndef FDTD_BATCH_MINB
+#define FDTD_BATCH_MINB 2
+#endif
+constexpr int kMaxBatch = 16;          // runs of one launch
+constexpr int kBatchThreads = 256;     // threads of a block of the persistent kernel
+constexpr int kMinBatchSZ = 4;         // z planes of a work item: 4 or 8 (<= kShellKZ) by grid size
+constexpr int kMaxBatchSlabs = 65536 / kMinBatchSZ + 1;
+static_assert(2 * kMinBatchSZ <= kShellKZ, "work items of up to kShellKZ planes");
+
+// One run of the batch, device-resident.
+template <typename T>
+struct BatchSlot {
+    KParams<T> kp[2];                  // the run's step parameters for even / odd steps
+    DParams<T> dp;                     // its running DFT (forward or adjoint accumulators)
+    unsigned* prog;                    // [nslab]: work items of the slab completed since the run started
+    int nslab, nxyc;                   // slabs of sz planes x chunks of cw (x, y) columns
+    int sz, cw;                        // work-item shape of this run
+    int n0;                            // first step of the current launch
+};
+
+// One launch: run j (in order of phases, descending) takes phases 0 .. nph[j]-1 of this launch, 2 per step
+// (H, E).  Work items are numbered round by round: round g holds phase g of every run with nph > g,
+// run by run, each run's items slab-major.  Segment q covers rounds [seg_g0[q], seg_g0[q+1]) in which the
+// first seg_m[q] runs take part; seg_t0[q] is its first item, seg_t0[nseg] the launch's item count.
+struct BatchLaunch {
+    int nruns, nseg;
+    int slot[kMaxBatch];               // slot of run j in the device table
+    long long pre[kMaxBatch + 1];      // items of one phase of runs 0 .. j-1
+    int seg_g0[kMaxBatch + 1];
+    int seg_m[kMaxBatch];
+    long long seg_t0[kMaxBatch + 1];
+    void* slots;                       // BatchSlot<T>[kMaxBatch]
+    unsigned long long* ticket;        // next work item (zeroed before every launch)
+    int* err;                          // [0]: 1 when a dependency wait gave up; [1]: the item that gave up
+    const int* gate;                   // test hook: non-null makes item 0 also wait for *gate != 0
+    unsigned long long wait_ns;        // limit of one dependency wait
+};
+
 // Paper-mode gradient, one checkpoint segment of forward levels n0..n0+len and adjoint levels
 // a0..a0+len (a0 = M - n0 - len): Eq. (Gradient_FDTD) accumulated per design voxel.
 template <typename T>

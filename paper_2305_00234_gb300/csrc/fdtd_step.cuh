@@ -522,17 +522,17 @@ __device__ __forceinline__ PsiCol psi_col(const KParams<T>& p, int x, int y, int
 // psi of one cell for the six curl terms (0 outside the slabs): [0] d/dy of the x row, [1] d/dy of
 // the z row (y slab); [2] d/dz of the x row, [3] d/dz of the y row (z slab); [4] d/dx of the y row,
 // [5] d/dx of the z row (x slab).
-template <typename T>
+template <typename T, bool CG>
 __device__ __forceinline__ void psi_load(T* const (&ps)[3][2], const PsiCol& pc, unsigned k, unsigned plane,
                                          unsigned col, int sx, int sy, int sz, T (&v)[6])
 {
     const unsigned q1 = k * pc.qys + pc.qy0, q2 = (unsigned)max(sz, 0) * plane + col, q0 = k * pc.qxs + pc.qx0;
-    v[0] = sy >= 0 ? ps[0][0][q1] : T(0);
-    v[1] = sy >= 0 ? ps[2][1][q1] : T(0);
-    v[2] = sz >= 0 ? ps[0][1][q2] : T(0);
-    v[3] = sz >= 0 ? ps[1][0][q2] : T(0);
-    v[4] = sx >= 0 ? ps[1][1][q0] : T(0);
-    v[5] = sx >= 0 ? ps[2][0][q0] : T(0);
+    v[0] = sy >= 0 ? ldf<CG>(ps[0][0] + q1) : T(0);
+    v[1] = sy >= 0 ? ldf<CG>(ps[2][1] + q1) : T(0);
+    v[2] = sz >= 0 ? ldf<CG>(ps[0][1] + q2) : T(0);
+    v[3] = sz >= 0 ? ldf<CG>(ps[1][0] + q2) : T(0);
+    v[4] = sx >= 0 ? ldf<CG>(ps[1][1] + q0) : T(0);
+    v[5] = sx >= 0 ? ldf<CG>(ps[2][0] + q0) : T(0);
 }
 
 template <typename T>
@@ -565,16 +565,15 @@ __device__ __forceinline__ T stretch_v(T d, const T* __restrict__ tab, int s, T&
     return add_rn(mul_rn(d, kinv), psi);
 }
 
-// H of the shell.  Within a batch every load is issued before any store (the buffers it writes are
-// not the ones it reads); E_x, E_y of the plane above a batch carry over as the next batch's own.
-template <typename T>
-__global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_h_kernel(const KParams<T> p, const ShellBoxes s)
+// H^{n+1/2} of one column (x, y), planes [k0, k1) (at most kShellKZ of them): every cell update of
+// the shell, CPML psi_H included.  Within a batch every load is issued before any store (the buffers
+// it writes are not the ones it reads); E_x, E_y of the plane above a batch carry over as the next
+// batch's own.  CG: state loads bypass L1 (for a persistent kernel whose earlier work items on the
+// same SM may hold stale lines).
+template <typename T, bool CG>
+__device__ __forceinline__ void h_column(const KParams<T>& p, int x, int y, int k0, int k1, int n)
 {
     constexpr int P = kShellPZ;
-    ShellCol cl;
-    if (!shell_cell(s, cl)) return;
-    const int x = cl.x, y = cl.y;
-    const int n = read_step<T>(p.ctl);
     const T cneg = -(p.ch * p.inv_dx), idx = p.inv_dx, ch = p.ch;
     const T einc_n = p.tfsf_i0 >= 0 ? __ldg(p.einc + n) : T(0);
     const bool tf = x == p.tfsf_i0 - 1;   // H_y here is scattered field
@@ -585,10 +584,10 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
     const T* __restrict__ E0 = p.E[0];
     const T* __restrict__ E1 = p.E[1];
     const T* __restrict__ E2 = p.E[2];
-    T exc = E0[(unsigned)cl.k0 * plane + col], eyc = E1[(unsigned)cl.k0 * plane + col];
-    for (int it = 0; it < kShellKZ / P; ++it) {   // compile-time trip bound; s.kz may end the column early
-        const int kb = cl.k0 + it * P;
-        if (kb >= cl.k1) break;
+    T exc = ldf<CG>(E0 + (unsigned)k0 * plane + col), eyc = ldf<CG>(E1 + (unsigned)k0 * plane + col);
+    for (int it = 0; it < kShellKZ / P; ++it) {   // compile-time trip bound; k1 may end the column early
+        const int kb = k0 + it * P;
+        if (kb >= k1) break;
         HIn<T> a[P];
         T ps[P][6];
         int sz[P];
@@ -596,27 +595,27 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
         for (int r = 0; r < P; ++r) {
             const int k = kb + r;
             sz[r] = slab_index(k, p.cpl[2], p.cph[2], p.nz);
-            if (k >= cl.k1) continue;
+            if (k >= k1) continue;
             const unsigned id = (unsigned)k * plane + col;
             const bool zp = k + 1 < p.nz;
             a[r].ex0 = r == 0 ? exc : a[r - 1].exz;
             a[r].ey0 = r == 0 ? eyc : a[r - 1].eyz;
-            a[r].ez0 = E2[id];
-            a[r].ezy = yp ? E2[id + nx] : T(0);
-            a[r].exy = yp ? E0[id + nx] : T(0);
-            a[r].ezx = xp ? E2[id + 1] : T(0);
-            a[r].eyx = xp ? E1[id + 1] : T(0);
-            a[r].exz = zp ? E0[id + plane] : T(0);
-            a[r].eyz = zp ? E1[id + plane] : T(0);
-            a[r].hox = p.H[0][id];
-            a[r].hoy = p.H[1][id];
-            a[r].hoz = p.H[2][id];
-            psi_load(p.psiH, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
+            a[r].ez0 = ldf<CG>(E2 + id);
+            a[r].ezy = yp ? ldf<CG>(E2 + id + nx) : T(0);
+            a[r].exy = yp ? ldf<CG>(E0 + id + nx) : T(0);
+            a[r].ezx = xp ? ldf<CG>(E2 + id + 1) : T(0);
+            a[r].eyx = xp ? ldf<CG>(E1 + id + 1) : T(0);
+            a[r].exz = zp ? ldf<CG>(E0 + id + plane) : T(0);
+            a[r].eyz = zp ? ldf<CG>(E1 + id + plane) : T(0);
+            a[r].hox = ldf<CG>(p.H[0] + id);
+            a[r].hoy = ldf<CG>(p.H[1] + id);
+            a[r].hoz = ldf<CG>(p.H[2] + id);
+            psi_load<T, CG>(p.psiH, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
         }
 #pragma unroll
         for (int r = 0; r < P; ++r) {
             const int k = kb + r;
-            if (k >= cl.k1) continue;
+            if (k >= k1) continue;
             const unsigned id = (unsigned)k * plane + col;
             const HIn<T>& c = a[r];
             T hx, hy, hz;
@@ -653,19 +652,25 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
     }
 }
 
-// E of the shell cells outside the design box, from H^{n+1/2} of the whole grid (after the interior
-// and shell H updates of the step); loads first within a batch, like the H kernel, with H_x, H_y of
-// the plane below a batch carried over.  It may run concurrently with the design-E kernel: the last
-// block of the two launches advances the step.
+// H of the shell: one thread per column of a shell box (see shell_cell).
 template <typename T>
-__global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_e_kernel(const KParams<T> p, const ShellBoxes s)
+__global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_h_kernel(const KParams<T> p, const ShellBoxes s)
+{
+    ShellCol cl;
+    if (!shell_cell(s, cl)) return;
+    h_column<T, false>(p, cl.x, cl.y, cl.k0, cl.k1, read_step<T>(p.ctl));
+}
+
+// E^{n+1} of the cells of one column (x, y), planes [k0, k1), that lie outside the working box, from
+// H^{n+1/2} of the whole grid (after every H update of the step); loads first within a batch, like
+// h_column, with H_x, H_y of the plane below a batch carried over.  Returns the largest |E| sum seen
+// on a checked step (0 otherwise).
+template <typename T, bool CG>
+__device__ __forceinline__ T e_column(const KParams<T>& p, int x, int y, int k0, int k1, int n)
 {
     constexpr int P = kShellPZ;
-    ShellCol cl;
-    const bool live = shell_cell(s, cl);
-    const int n = read_step<T>(p.ctl);
-    if (live) {
-        const int x = cl.x, y = cl.y;
+    T emax = T(0);
+    {
         const T hinc_n = p.tfsf_i0 >= 0 ? __ldg(p.hinc + n) : T(0);
         const bool check = (n & 15) == 0 || n + 1 == p.n_steps;
         const bool tf = x == p.tfsf_i0;   // H_y(i0-1/2) is scattered field
@@ -677,12 +682,11 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
         const T* __restrict__ H1 = p.Hn[1];
         const T* __restrict__ H2 = p.Hn[2];
         T hxb = T(0), hyb = T(0);   // H_x, H_y of the plane below the batch
-        if (cl.k0 > 0) {
-            hxb = H0[(unsigned)(cl.k0 - 1) * plane + col];
-            hyb = H1[(unsigned)(cl.k0 - 1) * plane + col];
+        if (k0 > 0) {
+            hxb = ldf<CG>(H0 + (unsigned)(k0 - 1) * plane + col);
+            hyb = ldf<CG>(H1 + (unsigned)(k0 - 1) * plane + col);
         }
-        T emax = T(0);
-        for (int kb = cl.k0; kb < cl.k1; kb += P) {   // (a compile-time trip bound here costs registers)
+        for (int kb = k0; kb < k1; kb += P) {   // (a compile-time trip bound here costs registers)
             T h[P][3], hm[P][4], e0[P][3], ps[P][6];
             bool on[P];
             int sz[P];
@@ -690,20 +694,20 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
             for (int r = 0; r < P; ++r) {
                 const int k = kb + r;
                 sz[r] = slab_index(k, p.cpl[2], p.cph[2], p.nz);
-                on[r] = k < cl.k1 && !(in_dxy && k >= p.db[4] && k < p.db[5]);
-                if (k >= cl.k1) continue;
+                on[r] = k < k1 && !(in_dxy && k >= p.db[4] && k < p.db[5]);
+                if (k >= k1) continue;
                 const unsigned id = (unsigned)k * plane + col;
-                h[r][0] = H0[id];
-                h[r][1] = H1[id];
-                h[r][2] = H2[id];
-                hm[r][0] = y > 0 ? H2[id - nx] : T(0);   // H_z(y-1)
-                hm[r][1] = y > 0 ? H0[id - nx] : T(0);   // H_x(y-1)
-                hm[r][2] = x > 0 ? H2[id - 1] : T(0);    // H_z(x-1)
-                hm[r][3] = x > 0 ? H1[id - 1] : T(0);    // H_y(x-1)
-                e0[r][0] = p.E[0][id];
-                e0[r][1] = p.E[1][id];
-                e0[r][2] = p.E[2][id];
-                psi_load(p.psiE, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
+                h[r][0] = ldf<CG>(H0 + id);
+                h[r][1] = ldf<CG>(H1 + id);
+                h[r][2] = ldf<CG>(H2 + id);
+                hm[r][0] = y > 0 ? ldf<CG>(H2 + id - nx) : T(0);   // H_z(y-1)
+                hm[r][1] = y > 0 ? ldf<CG>(H0 + id - nx) : T(0);   // H_x(y-1)
+                hm[r][2] = x > 0 ? ldf<CG>(H2 + id - 1) : T(0);    // H_z(x-1)
+                hm[r][3] = x > 0 ? ldf<CG>(H1 + id - 1) : T(0);    // H_y(x-1)
+                e0[r][0] = ldf<CG>(p.E[0] + id);
+                e0[r][1] = ldf<CG>(p.E[1] + id);
+                e0[r][2] = ldf<CG>(p.E[2] + id);
+                psi_load<T, CG>(p.psiE, pc, (unsigned)k, plane, col, sx, sy, sz[r], ps[r]);
             }
 #pragma unroll
             for (int r = 0; r < P; ++r) {
@@ -759,6 +763,20 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MIN
             hxb = h[P - 1][0];   // read only when plane kb + P is this thread's
             hyb = h[P - 1][1];
         }
+    }
+    return emax;
+}
+
+// E of the shell cells outside the design box.  It may run concurrently with the design-E kernel: the
+// last block of the two launches advances the step.
+template <typename T>
+__global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_e_kernel(const KParams<T> p, const ShellBoxes s)
+{
+    ShellCol cl;
+    const bool live = shell_cell(s, cl);
+    const int n = read_step<T>(p.ctl);
+    if (live) {
+        const T emax = e_column<T, false>(p, cl.x, cl.y, cl.k0, cl.k1, n);
         if (!(emax < p.blowup)) atomicOr(p.ctl + 2, 1);
     }
     finish_step(p.ctl, p.nblocks_e, n);

@@ -109,6 +109,11 @@ class Problem:
         N.fdtd_paper_gradient(self.h, out, pole_pairing)
         return out
 
+    def objective(self):
+        """(F, gap DFT) of the last forward run, batched or not."""
+        F, g = N.fdtd_get_objective(self.h, 2 * self.nf * 3 * self.ngap)
+        return F, (g[0::2] + 1j * g[1::2]).reshape((self.nf, 3) + self.gshape)
+
     def gradient_norm2(self):
         return N.fdtd_gradient_norm(self.h)
 
@@ -149,6 +154,51 @@ class Problem:
 
     def info(self):
         return N.fdtd_get_info(self.h)
+
+
+class Batch:
+    """Runs of several Problems advanced together by the persistent kernel (fdtd_batch_*)."""
+
+    def __init__(self, stream=None):
+        self.b = N.fdtd_batch_create(stream)
+        self.members = {}                       # handle value -> Problem
+
+    def submit(self, problem, adjoint=False):
+        """Start the problem's forward (or adjoint) run in the batch."""
+        if not adjoint:
+            problem.version += 1                # replaces the forward result the handle holds
+        N.fdtd_batch_submit(self.b, problem.h, adjoint)
+        self.members[problem.h.value] = problem
+
+    def run(self, max_steps):
+        """One launch; [(problem, status), ...] of the runs that ended (status 0 = ok)."""
+        out = []
+        for hv, st in N.fdtd_batch_run(self.b, max_steps):
+            out.append((self.members.pop(hv), st))
+        return out
+
+    def set_wait_limit(self, wait_ns, gate=False):
+        N.fdtd_batch_set_wait_limit(self.b, wait_ns, gate)
+
+    def info(self):
+        return N.fdtd_batch_info(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            N.fdtd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def problem(w, stream=None):

@@ -1,17 +1,23 @@
 """Continuous-batching server for gradient evaluations (serving workload).
 
-Requests of different grid sizes from concurrent optimisations arrive at any time.  The
-dispatcher admits a waiting request as soon as a slot is free and its device footprint
-(``fdtd_footprint_bytes``) fits the remaining HBM budget; every admitted request owns a handle
-(fields, CPML state, pole currents and DFTs resident on the device) and its own CUDA stream, and
-runs its forward / adjoint / gradient as captured CUDA graphs of 16 time steps.  Requests on the
-device therefore overlap: the GPU's hardware scheduler interleaves the blocks of every stream's
-graphs, which fills the 152 SMs even with grids (48^3 ... 192^3) too small to do it alone.
-Finished requests release their slot and memory immediately, and the next waiting request is
-admitted (continuous batching, FIFO among the waiting).
+Requests of different grid sizes from concurrent optimisations arrive at any time.  The dispatcher
+admits a waiting request (FIFO) as soon as a slot is free and its device footprint
+(``fdtd_footprint_bytes``) fits the remaining HBM budget; every admitted request owns a handle whose
+fields, CPML state, pole currents and DFTs stay resident on the device until its gradient is out.
+Admitted requests go to one of two lanes:
 
-Each result is bitwise independent of the mix: a request's state is private and every kernel is
-deterministic (no cross-request reductions or atomics on data).
+* the batch lane (grids up to ``batch_max_cells``): the forward and adjoint runs of every request in
+  the lane are advanced together by the persistent kernel (``fdtd_batch_run``: one captured CUDA graph
+  per launch, work items from a device work queue, up to ``chunk_steps`` steps of every run per launch).
+  Requests enter and leave between launches, so a request that arrives while others are on the GPU
+  joins the next launch;
+* the plain lane (larger grids, which fill the GPU on their own): each request runs its
+  forward / adjoint / gradient as 16-step CUDA graphs on a stream of its own, next to the batch lane's
+  launches.
+
+Finished requests release their slot and memory immediately and the next waiting one is admitted.
+Each result is bitwise independent of the mix: a request's state is private, every kernel is
+deterministic, and a batched run's arithmetic does not depend on which runs share its launches.
 """
 from __future__ import annotations
 
@@ -23,7 +29,7 @@ import time
 import numpy as np
 
 from . import _native as N
-from .problem import Problem
+from .problem import Batch, Problem
 
 
 class Request:
@@ -39,15 +45,19 @@ class Request:
     def footprint(self):
         return N.fdtd_footprint_bytes(self.desc, self.poles_total)
 
-    def cell_updates(self):
+    def cells(self):
         d = self.desc
-        return 2.0 * d["nx"] * d["ny"] * d["nz"] * d["n_steps"]
+        return d["nx"] * d["ny"] * d["nz"]
+
+    def cell_updates(self):
+        return 2.0 * self.cells() * self.desc["n_steps"]
 
 
 class Result:
-    def __init__(self, rid, F, grad, t_arrival, t_admit, t_done):
+    def __init__(self, rid, F, grad, t_arrival, t_admit, t_done, lane=""):
         self.id, self.F, self.grad = rid, F, grad
         self.t_arrival, self.t_admit, self.t_done = t_arrival, t_admit, t_done
+        self.lane = lane
 
     @property
     def latency(self):
@@ -55,7 +65,7 @@ class Result:
 
 
 def evaluate(req, stream=None):
-    """One gradient evaluation on the current device (no server)."""
+    """One gradient evaluation on the current device, plain path (no server)."""
     p = Problem(req.desc, req.bg, req.m1, req.m2, req.gamma, stream=stream)
     try:
         p.set_density(req.rho)
@@ -68,18 +78,26 @@ def evaluate(req, stream=None):
 
 
 class GradientServer:
-    """submit(request) -> Future[Result].  max_slots requests on the device at once, their summed
-    footprints within hbm_budget bytes."""
+    """submit(request) -> Future[Result].
 
-    def __init__(self, max_slots=8, hbm_budget=None, device=0):
+    max_slots requests on the device at once (at most 16 of them in the batch lane), their summed
+    footprints within hbm_budget bytes.  batch_max_cells: grids with at most this many cells take the
+    batch lane (0: every request takes the plain lane; None: every FP32 request takes the batch lane).
+    chunk_steps: steps of every batched run per persistent launch."""
+
+    def __init__(self, max_slots=16, hbm_budget=None, device=0, batch_max_cells=64 ** 3, chunk_steps=128,
+                 plain_workers=4):
         import torch
         self.torch = torch
         self.device = device
+        torch.cuda.set_device(device)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(device)
             hbm_budget = int(0.8 * free)
         self.hbm_budget = hbm_budget
         self.max_slots = max_slots
+        self.batch_max_cells = batch_max_cells
+        self.chunk_steps = chunk_steps
         self.cv = threading.Condition()
         self.waiting = collections.deque()
         self.in_use = 0
@@ -87,10 +105,17 @@ class GradientServer:
         self.closed = False
         self.peak_active = 0
         self.peak_in_use = 0
-        self.pool = cf.ThreadPoolExecutor(max_workers=max_slots)
-        self.dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self.peak_batched = 0
+        self.launches = 0
+        self.error = None
+        self.stream = torch.cuda.Stream(device=device)
+        self.batch = Batch(self.stream.cuda_stream)
+        self.in_batch = {}          # Problem -> (request, future, footprint, t_admit, phase)
+        self.plain_pool = cf.ThreadPoolExecutor(max_workers=plain_workers)
+        self.dispatcher = threading.Thread(target=self._loop, daemon=True)
         self.dispatcher.start()
 
+    # ---- public -------------------------------------------------------------------------------
     def submit(self, req):
         """Queue a request; an invalid or oversized one fails its own future, nothing else."""
         fut = cf.Future()
@@ -109,47 +134,14 @@ class GradientServer:
             self.cv.notify_all()
         return fut
 
-    def _can_admit(self):
-        return bool(self.waiting) and self.active < self.max_slots and \
-            self.in_use + self.waiting[0][1] <= self.hbm_budget
-
-    def _dispatch(self):
-        while True:
-            with self.cv:
-                while not self._can_admit():
-                    if self.closed and not self.waiting:
-                        return
-                    self.cv.wait()
-                req, fp, fut = self.waiting.popleft()
-                self.in_use += fp
-                self.active += 1
-                self.peak_active = max(self.peak_active, self.active)
-                self.peak_in_use = max(self.peak_in_use, self.in_use)
-            self.pool.submit(self._run, req, fp, fut, time.perf_counter())
-
-    def _run(self, req, fp, fut, t_admit):
-        torch = self.torch
-        try:
-            torch.cuda.set_device(self.device)
-            stream = torch.cuda.Stream(device=self.device)
-            F, g = evaluate(req, stream=stream.cuda_stream)
-            stream.synchronize()
-            fut.set_result(Result(req.id, F, g, req.t_arrival, t_admit, time.perf_counter()))
-        except Exception as e:  # the request fails, the server keeps serving
-            fut.set_exception(e)
-        finally:
-            with self.cv:
-                self.in_use -= fp
-                self.active -= 1
-                self.cv.notify_all()
-
     def close(self):
         """Serve everything already submitted, then stop."""
         with self.cv:
             self.closed = True
             self.cv.notify_all()
         self.dispatcher.join()
-        self.pool.shutdown(wait=True)
+        self.plain_pool.shutdown(wait=True)
+        self.batch.close()
 
     def __enter__(self):
         return self
@@ -157,11 +149,124 @@ class GradientServer:
     def __exit__(self, *exc):
         self.close()
 
+    # ---- dispatcher ---------------------------------------------------------------------------
+    def _batch_lane(self, req):
+        if req.desc.get("precision", 32) != 32:
+            return False
+        return self.batch_max_cells is None or req.cells() <= self.batch_max_cells
+
+    def _can_admit(self):
+        if not self.waiting or self.active >= self.max_slots:
+            return False
+        req, fp, _ = self.waiting[0]
+        if self.in_use + fp > self.hbm_budget:
+            return False
+        return not self._batch_lane(req) or len(self.in_batch) < N.MAX_BATCH
+
+    def _release(self, fp):
+        with self.cv:
+            self.in_use -= fp
+            self.active -= 1
+            self.cv.notify_all()
+
+    def _admit_one(self):
+        """Pop the first waiting request and start it in its lane (called with self.cv held)."""
+        req, fp, fut = self.waiting.popleft()
+        self.in_use += fp
+        self.active += 1
+        self.peak_active = max(self.peak_active, self.active)
+        self.peak_in_use = max(self.peak_in_use, self.in_use)
+        return req, fp, fut, time.perf_counter()
+
+    def _start_batched(self, req, fp, fut, t_admit):
+        try:
+            p = Problem(req.desc, req.bg, req.m1, req.m2, req.gamma, stream=self.stream.cuda_stream)
+            try:
+                p.set_density(req.rho)
+                self.batch.submit(p)
+            except Exception:
+                p.close()
+                raise
+        except Exception as e:
+            fut.set_exception(e)
+            self._release(fp)
+            return
+        self.in_batch[p] = [req, fut, fp, t_admit, 0]
+        self.peak_batched = max(self.peak_batched, len(self.in_batch))
+
+    def _run_plain(self, req, fp, fut, t_admit):
+        torch = self.torch
+        try:
+            torch.cuda.set_device(self.device)
+            stream = torch.cuda.Stream(device=self.device)
+            F, g = evaluate(req, stream=stream.cuda_stream)
+            stream.synchronize()
+            fut.set_result(Result(req.id, F, g, req.t_arrival, t_admit, time.perf_counter(), "plain"))
+        except Exception as e:  # the request fails, the server keeps serving
+            fut.set_exception(e)
+        finally:
+            self._release(fp)
+
+    def _finish_batched(self, p, status):
+        req, fut, fp, t_admit, phase = self.in_batch[p]
+        try:
+            if status != 0:
+                raise N.FdtdError(status, N.fdtd_last_error(p.h))
+            if phase == 0:                      # forward run ended: its adjoint run joins the next launch
+                self.batch.submit(p, adjoint=True)
+                self.in_batch[p][4] = 1
+                return
+            F, _ = p.objective()
+            g = p.gradient()
+            fut.set_result(Result(req.id, F, g, req.t_arrival, t_admit, time.perf_counter(), "batch"))
+        except Exception as e:
+            fut.set_exception(e)
+        del self.in_batch[p]
+        p.close()
+        self._release(fp)
+
+    def _loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        while True:
+            starts = []
+            with self.cv:
+                while True:
+                    while self._can_admit():
+                        starts.append(self._admit_one())
+                    if starts or self.in_batch:
+                        break
+                    if self.closed and not self.waiting and self.active == 0:
+                        return
+                    self.cv.wait()
+            for req, fp, fut, t_admit in starts:
+                if self._batch_lane(req):
+                    self._start_batched(req, fp, fut, t_admit)
+                else:
+                    self.plain_pool.submit(self._run_plain, req, fp, fut, t_admit)
+            if not self.in_batch:
+                continue
+            try:
+                done = self.batch.run(self.chunk_steps)
+            except Exception as e:             # the batch is dead: fail its requests, start a new one
+                self.error = e
+                for p, (req, fut, fp, t_admit, phase) in list(self.in_batch.items()):
+                    fut.set_exception(e)
+                    p.close()
+                    self._release(fp)
+                self.in_batch.clear()
+                self.batch.close()
+                self.batch = Batch(self.stream.cuda_stream)
+                continue
+            self.launches += 1
+            for p, st in done:
+                self._finish_batched(p, st)
+
 
 def replay_stream(requests, server=None, time_scale=1.0):
     """Submit requests at their (scaled) arrival times; return results in request order and the
     wall time from the first arrival to the last completion.  server=None runs them one after
-    another in arrival order on the calling thread (the sequential baseline)."""
+    another in arrival order on the calling thread (the sequential baseline, plain path)."""
     t0 = time.perf_counter()
     futs, results = [], []
     for r in requests:
@@ -173,7 +278,7 @@ def replay_stream(requests, server=None, time_scale=1.0):
         if server is None:
             start = time.perf_counter()
             F, g = evaluate(r)
-            results.append(Result(r.id, F, g, due, start, time.perf_counter()))
+            results.append(Result(r.id, F, g, due, start, time.perf_counter(), "sequential"))
         else:
             futs.append(server.submit(r))
     if server is not None:

@@ -1,5 +1,6 @@
-"""Serving loop: continuous batching with admission by device footprint; every result is the
-same alone and in the mix."""
+"""Serving loop: continuous batching with admission by device footprint, the batch lane (persistent kernel
+over a device work queue) and the plain lane (per-request streams); every result is the same alone and in
+the mix."""
 import numpy as np
 import pytest
 
@@ -19,22 +20,31 @@ def srv():
     return serve
 
 
-def small_stream(n=6, seed=7):
-    items = synth.serving_stream(seed=seed, n_requests=n, sizes=(48, 56, 64), steps=(300, 500),
-                                 pairs=(1, 3))
-    return items
+def small_stream(n=6, seed=7, sizes=(48, 56, 64)):
+    return synth.serving_stream(seed=seed, n_requests=n, sizes=sizes, steps=(300, 500), pairs=(1, 3))
 
 
-def test_alone_and_in_the_mix_are_bitwise_equal(srv):
+@pytest.mark.parametrize("batch_max_cells", [None, 0, 52 ** 3])
+def test_alone_and_in_the_mix_are_bitwise_equal(srv, batch_max_cells):
+    """batch_max_cells None: every request in the batch lane; 0: every request in the plain lane; 52^3:
+    both lanes at once.  Alone = the same server admitting one request at a time."""
     items = small_stream()
-    alone = [srv.evaluate(r) for r in srv.from_stream(items)]
-    with srv.GradientServer(max_slots=4) as server:
+    with srv.GradientServer(max_slots=1, batch_max_cells=batch_max_cells, chunk_steps=64) as server:
+        alone = [server.submit(r).result() for r in srv.from_stream(items)]
+    with srv.GradientServer(max_slots=6, batch_max_cells=batch_max_cells, chunk_steps=48) as server:
         futs = [server.submit(r) for r in srv.from_stream(items)]
         mixed = [f.result() for f in futs]
     assert server.peak_active >= 2            # the requests overlapped on the device
-    for (F, g), r in zip(alone, mixed):
-        assert F == r.F
-        assert np.array_equal(g, r.grad)
+    lanes = {r.lane for r in mixed}
+    assert lanes == {None: {"batch"}, 0: {"plain"}}.get(batch_max_cells, {"batch", "plain"})
+    for a, m, it in zip(alone, mixed, items):
+        assert a.F == m.F and a.lane == m.lane
+        assert np.array_equal(a.grad, m.grad)
+    # either lane gives the plain path's result to FP32 rounding
+    for m, r in zip(mixed, srv.from_stream(items)):
+        F, g = srv.evaluate(r)
+        assert abs(m.F - F) <= 1e-5 * abs(F)
+        assert np.linalg.norm(m.grad - g) <= 1e-5 * np.linalg.norm(g)
 
 
 def test_admission_by_footprint_and_failure_isolation(srv):
@@ -58,3 +68,18 @@ def test_admission_by_footprint_and_failure_isolation(srv):
         f_big.result()
     assert "budget" in str(e.value)
     assert all(r.F > 0 for r in res)
+
+
+def test_requests_arriving_during_a_launch_join_the_next_one(srv):
+    """Continuous batching: requests submitted while the batch lane is running enter its later launches
+    (the batch held more runs at once than were submitted before the first launch)."""
+    items = small_stream(6, seed=19, sizes=(48,))
+    reqs = srv.from_stream(items)
+    with srv.GradientServer(max_slots=8, batch_max_cells=None, chunk_steps=32) as server:
+        futs = [server.submit(reqs[0])]
+        import time
+        time.sleep(0.05)
+        futs += [server.submit(r) for r in reqs[1:]]
+        res = [f.result() for f in futs]
+    assert all(r.lane == "batch" for r in res)
+    assert server.peak_batched >= 2 and server.launches >= 2
