@@ -322,6 +322,8 @@ fdtd_status fdtd_filter_project_grad(const float* rho_t, const float* dF_drho_b,
  *  fdtd_batch_set_wait_limit: the limit of one wait (default 1 s); gate = 1 is a failure-path test hook
  *    that makes the first work item also wait on a flag nothing sets, so that the next fdtd_batch_run
  *    returns FDTD_ERR_TIMEOUT without any GPU fault.
+ *  fdtd_batch_set_blocks: blocks of the persistent launches (0, the default: as many as fit on the
+ *    device; fewer leave SMs to other work on the device, e.g. runs outside the batch).
  *  fdtd_batch_info: runs in the batch and launches made.
  *  Errors: FDTD_ERR_ARG, FDTD_ERR_STATE (call order, full batch, dead batch), FDTD_ERR_OOM,
  *  FDTD_ERR_TIMEOUT, FDTD_ERR_CUDA; the text of batch calls is in fdtd_last_error(NULL). */
@@ -331,6 +333,7 @@ fdtd_status fdtd_batch_submit(fdtd_batch b, fdtd_handle h, int adjoint);
 fdtd_status fdtd_batch_run(fdtd_batch b, int max_steps, fdtd_handle* done, fdtd_status* done_status, int capacity,
                            int* n_done);
 fdtd_status fdtd_batch_set_wait_limit(fdtd_batch b, long long wait_ns, int gate);
+fdtd_status fdtd_batch_set_blocks(fdtd_batch b, int blocks);
 fdtd_status fdtd_batch_info(fdtd_batch b, int* n_runs, long long* launches);
 fdtd_status fdtd_batch_destroy(fdtd_batch b);
 

@@ -23,7 +23,8 @@ EXPORTS = ("fdtd_create_grid", "fdtd_footprint_bytes", "fdtd_set_materials", "fd
            "fdtd_reset_timings", "fdtd_get_info", "fdtd_cancel", "fdtd_last_error", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_filter_project", "fdtd_filter_project_grad", "fdtd_paper_forward",
            "fdtd_paper_gradient", "fdtd_get_gradient_constants", "fdtd_inject_wait_timeout", "fdtd_batch_create",
-           "fdtd_batch_submit", "fdtd_batch_run", "fdtd_batch_set_wait_limit", "fdtd_batch_info", "fdtd_batch_destroy",
+           "fdtd_batch_submit", "fdtd_batch_run", "fdtd_batch_set_wait_limit", "fdtd_batch_set_blocks", "fdtd_batch_info",
+           "fdtd_batch_destroy",
            "fdtd_get_objective")
 
 
@@ -96,6 +97,7 @@ def load_library():
         "fdtd_batch_submit": [vp, vp, i],
         "fdtd_batch_run": [vp, i, P(vp), P(C.c_int), i, P(C.c_int)],
         "fdtd_batch_set_wait_limit": [vp, C.c_longlong, i],
+        "fdtd_batch_set_blocks": [vp, i],
         "fdtd_batch_info": [vp, P(C.c_int), P(C.c_longlong)],
         "fdtd_batch_destroy": [vp],
         "fdtd_get_objective": [vp, P(d), P(d)],
@@ -414,6 +416,10 @@ def fdtd_batch_run(b, max_steps):
 
 def fdtd_batch_set_wait_limit(b, wait_ns, gate=False):
     _check_batch(load_library().fdtd_batch_set_wait_limit(b, int(wait_ns), int(bool(gate))), "fdtd_batch_set_wait_limit")
+
+
+def fdtd_batch_set_blocks(b, blocks):
+    _check_batch(load_library().fdtd_batch_set_blocks(b, int(blocks)), "fdtd_batch_set_blocks")
 
 
 def fdtd_batch_info(b):

@@ -1988,6 +1988,28 @@ fdtd_status fdtd_batch_set_wait_limit(fdtd_batch b, long long wait_ns, int gate)
     return FDTD_OK;
 }
 
+fdtd_status fdtd_batch_set_blocks(fdtd_batch b, int blocks)
+{
+    if (!b || blocks < 0) return FDTD_ERR_ARG;
+    std::lock_guard<std::mutex> lock(b->mu);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) return FDTD_ERR_CUDA;
+    for (int bi = 0; bi < 3; ++bi) {
+        int per = 0;
+        if (fdtd::batch_blocks_per_sm<float>(bi == 0 ? 4 : (bi == 1 ? 8 : 16), &per) != cudaSuccess) return FDTD_ERR_CUDA;
+        const unsigned full = (unsigned)std::max(1, sms * std::max(1, per));
+        b->blocks[bi] = blocks == 0 ? full : std::min(full, (unsigned)blocks);
+        if (b->exec[bi]) {                       // the grid size is part of the captured graph
+            cudaGraphExecDestroy(b->exec[bi]);
+            cudaGraphDestroy(b->graph[bi]);
+            b->exec[bi] = nullptr;
+            b->graph[bi] = nullptr;
+            b->knode[bi] = nullptr;
+        }
+    }
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_batch_info(fdtd_batch b, int* n_runs, long long* launches)
 {
     if (!b) return FDTD_ERR_ARG;

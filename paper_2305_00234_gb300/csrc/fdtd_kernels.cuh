@@ -42,10 +42,33 @@ __device__ __forceinline__ long long psi_index(const KParams<T>& p, int i, int j
 }
 
 // CFS-CPML: psi <- b psi + c d ; derivative -> d / kappa + psi.
+#ifndef FDTD_PML4
+#define FDTD_PML4 1
+#endif
+// {1/kappa, b, c} of slab index s from a table of 4 values per index (FP32: one 16-byte load with
+// FDTD_PML4, the default)
+template <typename T>
+__device__ __forceinline__ void pml_coef(const T* __restrict__ tab, int s, T& kinv, T& b, T& c)
+{
+#if FDTD_PML4
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(tab) + s);
+        kinv = v.x;
+        b = v.y;
+        c = v.z;
+        return;
+    }
+#endif
+    kinv = __ldg(tab + 4 * s);
+    b = __ldg(tab + 4 * s + 1);
+    c = __ldg(tab + 4 * s + 2);
+}
+
 template <typename T>
 __device__ __forceinline__ T stretch(T d, const T* __restrict__ tab, int s, T* psi)
 {
-    const T kinv = __ldg(tab + 4 * s), b = __ldg(tab + 4 * s + 1), c = __ldg(tab + 4 * s + 2);
+    T kinv, b, c;
+    pml_coef(tab, s, kinv, b, c);
     const T v = b * (*psi) + c * d;
     *psi = v;
     return d * kinv + v;
@@ -53,6 +76,22 @@ __device__ __forceinline__ T stretch(T d, const T* __restrict__ tab, int s, T* p
 
 template <typename T>
 __device__ __forceinline__ T ldg_t(const T* p) { return __ldg(p); }
+
+#ifndef FDTD_ED_FASTDIV
+#define FDTD_ED_FASTDIV 1
+#endif
+// a / b of the design update: in FP32 (FDTD_ED_FASTDIV, default) the hardware reciprocal and a multiply,
+// at most 2 ulp for normal b (D is a positive normal number here; measured 4% faster than the IEEE
+// division); in FP64, and with FDTD_ED_FASTDIV 0, the IEEE division
+__device__ __forceinline__ float div_t(float a, float b)
+{
+#if FDTD_ED_FASTDIV
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
 
 // Load of solver state (fields, psi, pole currents, density, snapshots, DFT accumulators).  CG: through
 // L2 only, bypassing L1, for work items of a persistent kernel, where an earlier item on the same SM may
@@ -110,7 +149,7 @@ __device__ __forceinline__ T design_update(const KParams<T>& p, const PoleTable<
     const T gm = p.hg * rho * (one - rho);
     const T D = p.D1[C] + rho * p.dD[C] + gm;
     const T N = p.N1[C] + rho * p.dN[C] - gm;
-    if (MP == 0) return (N * e_old + drive) / D;
+    if (MP == 0) return div_t(N * e_old + drive, D);
     const int P = p.P[C], P1 = p.P1[C];
     cpx<T>* __restrict__ Q = p.Q[C];
     T sq = T(0);
@@ -122,7 +161,7 @@ __device__ __forceinline__ T design_update(const KParams<T>& p, const PoleTable<
             sq += kap * (g.re * q[pp].re - g.im * q[pp].im);
         }
     }
-    const T e_new = (N * e_old + drive - sq) / D;
+    const T e_new = div_t(N * e_old + drive - sq, D);
     const T es = e_new + e_old;
 #pragma unroll
     for (int pp = 0; pp < MP; ++pp) {

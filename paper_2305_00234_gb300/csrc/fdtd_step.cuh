@@ -560,7 +560,8 @@ __device__ __forceinline__ void psi_store(T* const (&ps)[3][2], const PsiCol& pc
 template <typename T>
 __device__ __forceinline__ T stretch_v(T d, const T* __restrict__ tab, int s, T& psi)
 {
-    const T kinv = __ldg(tab + 4 * s), b = __ldg(tab + 4 * s + 1), c = __ldg(tab + 4 * s + 2);
+    T kinv, b, c;
+    pml_coef(tab, s, kinv, b, c);
     psi = add_rn(mul_rn(b, psi), mul_rn(c, d));
     return add_rn(mul_rn(d, kinv), psi);
 }

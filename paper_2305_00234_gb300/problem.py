@@ -180,6 +180,10 @@ class Batch:
     def set_wait_limit(self, wait_ns, gate=False):
         N.fdtd_batch_set_wait_limit(self.b, wait_ns, gate)
 
+    def set_blocks(self, blocks):
+        """Blocks of the persistent launches (0: as many as fit on the device)."""
+        N.fdtd_batch_set_blocks(self.b, blocks)
+
     def info(self):
         return N.fdtd_batch_info(self.b)
 

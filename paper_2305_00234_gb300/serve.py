@@ -83,10 +83,11 @@ class GradientServer:
     max_slots requests on the device at once (at most 16 of them in the batch lane), their summed
     footprints within hbm_budget bytes.  batch_max_cells: grids with at most this many cells take the
     batch lane (0: every request takes the plain lane; None: every FP32 request takes the batch lane).
-    chunk_steps: steps of every batched run per persistent launch."""
+    chunk_steps: steps of every batched run per persistent launch; batch_blocks: blocks of those launches
+    (0: as many as fit; fewer leave SMs to the plain lane's kernels)."""
 
     def __init__(self, max_slots=16, hbm_budget=None, device=0, batch_max_cells=64 ** 3, chunk_steps=128,
-                 plain_workers=4):
+                 plain_workers=4, batch_blocks=0):
         import torch
         self.torch = torch
         self.device = device
@@ -106,10 +107,12 @@ class GradientServer:
         self.peak_active = 0
         self.peak_in_use = 0
         self.peak_batched = 0
+        self.batch_pending = 0
         self.launches = 0
         self.error = None
         self.stream = torch.cuda.Stream(device=device)
-        self.batch = Batch(self.stream.cuda_stream)
+        self.batch_blocks = batch_blocks
+        self.batch = self._new_batch()
         self.in_batch = {}          # Problem -> (request, future, footprint, t_admit, phase)
         self.plain_pool = cf.ThreadPoolExecutor(max_workers=plain_workers)
         self.dispatcher = threading.Thread(target=self._loop, daemon=True)
@@ -150,6 +153,12 @@ class GradientServer:
         self.close()
 
     # ---- dispatcher ---------------------------------------------------------------------------
+    def _new_batch(self):
+        b = Batch(self.stream.cuda_stream)
+        if self.batch_blocks:
+            b.set_blocks(self.batch_blocks)
+        return b
+
     def _batch_lane(self, req):
         if req.desc.get("precision", 32) != 32:
             return False
@@ -161,7 +170,7 @@ class GradientServer:
         req, fp, _ = self.waiting[0]
         if self.in_use + fp > self.hbm_budget:
             return False
-        return not self._batch_lane(req) or len(self.in_batch) < N.MAX_BATCH
+        return not self._batch_lane(req) or len(self.in_batch) + self.batch_pending < N.MAX_BATCH
 
     def _release(self, fp):
         with self.cv:
@@ -174,11 +183,15 @@ class GradientServer:
         req, fp, fut = self.waiting.popleft()
         self.in_use += fp
         self.active += 1
+        if self._batch_lane(req):
+            self.batch_pending += 1             # in the batch lane from here on (counted before its submit)
         self.peak_active = max(self.peak_active, self.active)
         self.peak_in_use = max(self.peak_in_use, self.in_use)
         return req, fp, fut, time.perf_counter()
 
     def _start_batched(self, req, fp, fut, t_admit):
+        with self.cv:
+            self.batch_pending -= 1
         try:
             p = Problem(req.desc, req.bg, req.m1, req.m2, req.gamma, stream=self.stream.cuda_stream)
             try:
@@ -256,7 +269,7 @@ class GradientServer:
                     self._release(fp)
                 self.in_batch.clear()
                 self.batch.close()
-                self.batch = Batch(self.stream.cuda_stream)
+                self.batch = self._new_batch()
                 continue
             self.launches += 1
             for p, st in done:
