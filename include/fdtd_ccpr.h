@@ -134,6 +134,8 @@ typedef struct {
                                                 0: the shell kernels cover the whole grid */
     double interior_cells;                   /* cells of the interior box (one fused-kernel launch) */
     double interior_design_cells;            /* of which inside the working box (no E update there) */
+    long long paired_shell;                  /* 1: the shell kernels update x-adjacent cell pairs (FP32, every
+                                                x bound of the grid, the x CPML and the shell boxes even) */
 } fdtd_timings;
 
 /* Create a problem on the given CUDA stream (cudaStream_t; NULL = default stream) of the current

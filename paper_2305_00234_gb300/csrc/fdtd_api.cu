@@ -314,6 +314,7 @@ struct SolverBase {
     virtual ~SolverBase() = default;
     virtual void interior_box(int ib[6]) const = 0;
     virtual bool has_interior() const = 0;
+    virtual bool paired_shell() const = 0;
 };
 
 struct fdtd_ctx {
@@ -402,6 +403,7 @@ struct Solver : SolverBase {
     explicit Solver(fdtd_ctx* ctx) : c(ctx) {}
     void interior_box(int ib[6]) const override { std::copy(base.ib, base.ib + 6, ib); }
     bool has_interior() const override { return fused; }
+    bool paired_shell() const override { return shell.pair != 0; }
     ~Solver() override
     {
         for (auto& g : graph)
@@ -539,6 +541,7 @@ struct Solver : SolverBase {
         CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), c->work));
         p.ctl = ctl;
         for (int m = 0; m < 2; ++m) dp[m].ctl = ctl;
+        shell.pair = shell_pairable(p) ? 1 : 0;
         p.nblocks_s = fdtd::shell_blocks(shell);
         p.edz = 1;
         p.nblocks_d = c->nd ? fdtd::design_blocks(c->dn[0], c->dn[1], c->dn[2], p.edz) : 0;
@@ -772,6 +775,17 @@ struct Solver : SolverBase {
             add(0, ib[0], ib[2], ib[3], ib[4], ib[5]);            // left and right of it in x
             add(ib[1], d.nx, ib[2], ib[3], ib[4], ib[5]);
         }
+    }
+
+    // The paired shell kernels (FP32) need the x boundaries of the grid, of the CPML slabs and of the
+    // shell boxes even (the two cells of a pair on the same side of each); the working box's x bounds,
+    // the TF/SF plane and point sources may fall between the cells of a pair.
+    bool shell_pairable(const KParams<T>& p) const
+    {
+        if (sizeof(T) != 4 || p.nx % 2 || p.cpl[0] % 2 || p.cph[0] % 2) return false;
+        for (int q = 0; q < shell.n; ++q)
+            if (shell.b[q][0] % 2 || shell.b[q][1] % 2) return false;
+        return true;
     }
 
     // Background part of one step: H of the shell and the fused interior (both read only the old
@@ -2333,6 +2347,7 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     if (!out) return FDTD_ERR_ARG;
     fdtd_timings t = h->tim;
     t.fused_step = h->impl && h->impl->has_interior() ? 1 : 0;
+    t.paired_shell = h->impl && h->impl->paired_shell() ? 1 : 0;
     const double ts = h->d.precision == 64 ? 8.0 : 4.0;
     // algorithmic bytes per launch: every state word read once and written once
     const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);

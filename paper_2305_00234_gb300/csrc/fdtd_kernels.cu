@@ -1,7 +1,8 @@
 // Launch wrappers and helper kernels; explicit FP32 / FP64 instantiations.
 #include "fdtd_kernels.cuh"
-#include "fdtd_step.cuh"
 #include "fdtd_launch.h"
+#include "fdtd_shell2.cuh"
+#include "fdtd_step.cuh"
 
 namespace fdtd {
 
@@ -116,7 +117,7 @@ unsigned shell_blocks(ShellBoxes& s)
         for (int q = 0; q < s.n; ++q) {
             const int* B = s.b[q];
             s.first[q] = t;
-            const unsigned wxy = (unsigned)(B[1] - B[0]) * (unsigned)(B[3] - B[2]);
+            const unsigned wxy = (unsigned)(B[1] - B[0]) / (s.pair ? 2u : 1u) * (unsigned)(B[3] - B[2]);
             t += (wxy + kShellCells - 1) / kShellCells * (unsigned)((B[5] - B[4] + s.kz - 1) / s.kz);
         }
         s.first[s.n] = t;
@@ -130,6 +131,15 @@ cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, 
 {
     const unsigned nb = s.first[s.n];
     if (nb == 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (s.pair) {
+            if (e_part)
+                shell_e2_kernel<<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
+            else
+                shell_h2_kernel<<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
+            return cudaGetLastError();
+        }
+    }
     if (e_part)
         shell_e_kernel<T><<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
     else

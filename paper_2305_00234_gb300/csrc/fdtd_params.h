@@ -91,6 +91,7 @@ struct ShellBoxes {
     int b[6][6];          // half-open x0, x1, y0, y1, z0, z1
     unsigned first[7];
     int kz;               // z planes per thread (<= kShellKZ)
+    int pair;             // 1: the paired kernels (a thread per two x-adjacent columns; every x bound even)
 };
 
 // Tensor maps of the buffers one step reads: E^n and H^{n-1/2}, each 4-D (x, y, z, component).

@@ -321,6 +321,30 @@ def test_cancel_flag_resets_per_call(gpu):
     p.close()
 
 
+@pytest.mark.parametrize("src", ["tfsf_odd", "tfsf_even", "dipole_shell_odd", "dipole_shell_even", "per_sample"])
+def test_paired_shell_paths(gpu, src):
+    """The paired FP32 shell kernels (two x-adjacent cells per thread): x CPML of even thickness on an even
+    grid, so that the shell boxes' x bounds are even; the design box's x bounds odd (pairs straddle the
+    working box in the shell E kernel), the TF/SF plane on either cell of a pair, a dipole in the shell on
+    either cell of a pair, and the per-sample density layout (working box grown by one on +x)."""
+    kw = {"tfsf_odd": dict(src_kind=1, src_pos=(9, 0, 0)), "tfsf_even": dict(src_kind=1, src_pos=(10, 0, 0)),
+          "dipole_shell_odd": dict(src_kind=0, src_comp=2, src_pos=(43, 20, 6)),
+          "dipole_shell_even": dict(src_kind=0, src_comp=1, src_pos=(4, 33, 18)),
+          "per_sample": dict(src_kind=1, src_pos=(9, 0, 0))}[src]
+    d = base_desc(52, 42, 37, n_steps=420, cpml=(6, 4, 4, 7, 5, 3), precision=32,
+                  design=(21, 18, 15), gap=(2, 2, 2), lambdas_nm=(500.0, 650.0), **kw)
+    assert d["design_box"][0] % 2 == 1
+    rho = synth.smooth_rho(synth.box_shape(d["design_box"]), 23, 2.0)
+    w = dict(desc=d, bg=vacuum(), m1=vacuum(), m2=synth.drude_lorentz_metal(23, 3), gamma=1e6, rho=rho)
+    per_voxel = src != "per_sample"
+    if not per_voxel:
+        w = per_sample(w, 31)
+    g = run_gpu(gpu, w)
+    t = g["p"].timings()
+    assert t["fused_step"] == 1 and t["paired_shell"] == 1
+    compare(g, run_oracle(w), 32, per_voxel=per_voxel)
+
+
 def per_sample(w, seed):
     """The same case with one density per E sample (density_layout 1): a seeded vector of
     N~ = sum_k prod_l (N_l + 1 - delta_kl) values (Sec. "FDTD implementation and design export")."""
