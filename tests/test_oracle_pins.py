@@ -440,20 +440,54 @@ def test_dispersive_half_space_reflection():
 # field as in a box large enough that nothing returns within the window.
 # ----------------------------------------------------------------------------------------------
 def test_cpml_absorbs():
-    M = 700
-    small = base_desc(24, 24, 24, dx=10e-9, n_steps=M, cpml=8, precision=64, src_pos=(12, 12, 12))
-    big = base_desc(120, 120, 120, dx=10e-9, n_steps=M, cpml=0, precision=64, src_pos=(60, 60, 60))
-    os_ = _oracle(small)
-    ob = _oracle(big)
-    ts_s, ts_b = [], []
-    for n in range(0, M, 10):
-        os_.step(n, 10, 1)
-        ob.step(n, 10, 1)
-        ts_s.append(os_.get_field(2)[12, 12, 14])
-        ts_b.append(ob.get_field(2)[60, 60, 62])
-    ts_s, ts_b = np.array(ts_s), np.array(ts_b)
-    err = np.abs(ts_s - ts_b).max() / np.abs(ts_b).max()
-    assert err < 2e-2
+    """3-D: a dipole pulse in a 40^3 box with a 12-cell CPML against the same pulse in a 140^3 box without
+    one, at a probe 3 cells from the source, over the 190 steps before the large box's PEC walls can echo
+    back (round trip 140 cells at c dt / dx = 0.57 cells per step): what the CPML reflects, including its
+    edges and corners at grazing incidence, stays below 2e-4 of the peak (measured 2.6e-5)."""
+    M = 190
+
+    def probe(n, cp):
+        c = n // 2
+        d = base_desc(n, n, n, dx=10e-9, n_steps=M, cpml=cp, precision=64, src_pos=(c, c, c))
+        dt = d["courant"] * d["dx"] / C0
+        d.update(src_fwhm_hz=2.0e15, src_t0=40 * dt)
+        o = _oracle(d)
+        ts = []
+        for n0 in range(0, M, 2):
+            o.step(n0, 2, 1)
+            ts.append(o.get_field(2)[c, c, c + 3])
+        o.close()
+        return np.array(ts)
+
+    small, big = probe(40, 12), probe(140, 0)
+    assert np.abs(big).max() > 0
+    assert np.abs(small - big).max() <= 2e-4 * np.abs(big).max()
+
+
+def test_cpml_normal_incidence_reflection():
+    """1-D: the TF/SF plane wave in a box periodic in y and z (so the fields are uniform there) hits the
+    +x CPML at normal incidence; the field the CPML sends back into the scattered-field region, 3 cells
+    before the plane, against the incident field 3 cells after it.  A graded CFS-CPML of 12 or 16 cells
+    reflects below 1e-4 (measured 1.6e-5 and 6.8e-6), and the thicker layer reflects less.  A half-cell
+    shift of the grading between the E and H positions reflects 6-8% here, a profile graded from the
+    wrong side about 75%."""
+    M = 1600
+    r = {}
+    for cp in (12, 16):
+        i0 = cp + 20
+        d = base_desc(2 * cp + 40, 4, 4, dx=10e-9, n_steps=M, cpml=(cp, cp, 0, 0, 0, 0), precision=64,
+                      bc=(0, 1, 1), src_kind=1, src_pos=(i0, 0, 0))
+        o = _oracle(d)
+        refl, inc = [], []
+        for n0 in range(M):
+            o.step(n0, 1, 1)
+            E = o.get_field(2)
+            refl.append(E[2, 2, i0 - 3])
+            inc.append(E[2, 2, i0 + 3])
+        o.close()
+        r[cp] = np.abs(refl).max() / np.abs(inc).max()
+        assert 0 < r[cp] < 1e-4, (cp, r[cp])
+    assert r[16] < r[12]
 
 
 # ----------------------------------------------------------------------------------------------
