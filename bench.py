@@ -404,10 +404,11 @@ def precision_study(args):
 
 def filter_bench(args):
     """fdtd_filter_project + fdtd_filter_project_grad on the design box (the paper's R = 12 cells, its
-    final beta = 52, eta = 0.5): CUDA-event time per forward + chain-rule pair.  Each call runs two
-    cone correlations (normalising sums, then the filter / its transpose); the algorithmic work is one
-    FMA per sphere tap (|d| < R) per voxel per correlation, against the FP32 FMA rate of the SMs
-    (152 SMs x 128 lanes x 2 flop x the sampled SM clock)."""
+    final beta = 52, eta = 0.5): CUDA-event time per forward + chain-rule pair.  Each call runs one cone
+    correlation (the filter, or its transpose) and the normalising sums, which come in closed form from a
+    summed-volume table of the weights; the algorithmic work is one FMA per sphere tap (|d| < R) per voxel
+    per correlation, against the FP32 FMA rate of the SMs (152 SMs x 128 lanes x 2 flop x the sampled SM
+    clock)."""
     import numpy as np
     import torch
 
@@ -440,7 +441,7 @@ def filter_bench(args):
     d = np.arange(-n, n + 1)
     taps = int(np.count_nonzero(np.sqrt(d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2) < R))
     nv = int(np.prod(shape))
-    flops = 2.0 * taps * nv * 4
+    flops = 2.0 * taps * nv * 2
     mhz = clk.get("sm_mhz") or 2070.0
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     line = {"metric": "density filter + projection and chain rule (cone R = 12)", "value": ms, "unit": "ms",
