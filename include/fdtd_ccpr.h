@@ -136,6 +136,8 @@ typedef struct {
     double interior_design_cells;            /* of which inside the working box (no E update there) */
     long long paired_shell;                  /* 1: the shell kernels update x-adjacent cell pairs (FP32, every
                                                 x bound of the grid, the x CPML and the shell boxes even) */
+    long long pdl_graphs;                    /* 1: the step graphs link each phase to the next through
+                                                programmatic dependent launch edges; 0: ordinary edges */
 } fdtd_timings;
 
 /* Create a problem on the given CUDA stream (cudaStream_t; NULL = default stream) of the current

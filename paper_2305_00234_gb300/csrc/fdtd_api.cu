@@ -315,6 +315,7 @@ struct SolverBase {
     virtual void interior_box(int ib[6]) const = 0;
     virtual bool has_interior() const = 0;
     virtual bool paired_shell() const = 0;
+    virtual bool pdl_graphs() const = 0;
 };
 
 struct fdtd_ctx {
@@ -393,6 +394,7 @@ struct Solver : SolverBase {
     int* ctl = nullptr;
     int ptot[3] = {0, 0, 0};
     bool fused = false;             // an interior box for the fused TMA step kernel exists
+    bool use_pdl = true;            // step graphs with programmatic edges between phases (else captured)
     StepMaps maps[2]{};             // tensor maps of the buffers read by even / odd steps
     fdtd::ShellBoxes shell{};       // the cells around the interior box
     std::vector<double2> ab_host;
@@ -404,6 +406,7 @@ struct Solver : SolverBase {
     void interior_box(int ib[6]) const override { std::copy(base.ib, base.ib + 6, ib); }
     bool has_interior() const override { return fused; }
     bool paired_shell() const override { return shell.pair != 0; }
+    bool pdl_graphs() const override { return use_pdl && graph[0][0] != nullptr; }
     ~Solver() override
     {
         for (auto& g : graph)
@@ -1193,8 +1196,73 @@ struct Solver : SolverBase {
         CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(int), s));
     }
 
+    // The graph of `steps` steps and one DFT launch, built node by node: per step an H phase (shell H
+    // kernel, fused interior kernel) and an E phase (shell E kernel, design-E kernel), the two kernels of a
+    // phase independent of each other, every kernel of a phase depending on both kernels of the phase
+    // before through a programmatic edge.  A phase's blocks are thereby launched while the phase before
+    // drains and wait (pdl_wait) until it has completed, instead of being launched after it.  Returns
+    // nullptr (and leaves no error state) where the driver refuses such a graph.
+    cudaGraphExec_t build_pdl_graph(int mode, int steps)
+    {
+        const KParams<T>& p = mode ? pa : pf;
+        cudaGraph_t g = nullptr;
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaGraphEdgeData ed = {};
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        std::vector<cudaGraphNode_t> prev, cur;
+        cudaError_t e = cudaSuccess;
+        auto link = [&](cudaGraphNode_t to) {
+            for (cudaGraphNode_t from : prev)
+                if (e == cudaSuccess) e = cudaGraphAddDependencies(g, &from, &to, &ed, 1);
+        };
+        auto phase = [&](auto&& add) {
+            cur.clear();
+            add();
+            for (cudaGraphNode_t n : cur) link(n);
+            prev = cur;
+        };
+        for (int st = 0; st < steps && e == cudaSuccess; ++st) {
+            const KParams<T> q = par(p, st);
+            phase([&] {
+                cudaGraphNode_t n = nullptr;
+                if (e == cudaSuccess && (e = fdtd::graph_shell<T>(g, &n, q, shell, false)) == cudaSuccess) cur.push_back(n);
+                if (e == cudaSuccess && fused && (e = fdtd::graph_step<T>(g, &n, q, maps[st & 1])) == cudaSuccess) cur.push_back(n);
+            });
+            phase([&] {
+                cudaGraphNode_t n = nullptr;
+                if (e == cudaSuccess && (e = fdtd::graph_shell<T>(g, &n, q, shell, true)) == cudaSuccess) cur.push_back(n);
+                if (e == cudaSuccess && c->nd && (e = fdtd::graph_e_design<T>(g, &n, q, htab, bucket)) == cudaSuccess)
+                    cur.push_back(n);
+            });
+        }
+        if (e == cudaSuccess && c->nd)
+            phase([&] {
+                cudaGraphNode_t n = nullptr;
+                if ((e = fdtd::graph_dft<T>(g, &n, dp[mode], steps)) == cudaSuccess) cur.push_back(n);
+            });
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return ex;
+    }
+
     void capture(int mode, int which, int steps)
     {
+        if (use_pdl) {
+            if (cudaGraphExec_t ex = build_pdl_graph(mode, steps)) {
+                graph[mode][which] = ex;
+                return;
+            }
+            use_pdl = false;    // the driver refused the programmatic edges: captured graphs from here on
+        }
         const KParams<T>& p = mode ? pa : pf;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
@@ -2348,6 +2416,7 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     fdtd_timings t = h->tim;
     t.fused_step = h->impl && h->impl->has_interior() ? 1 : 0;
     t.paired_shell = h->impl && h->impl->paired_shell() ? 1 : 0;
+    t.pdl_graphs = h->impl && h->impl->pdl_graphs() ? 1 : 0;
     const double ts = h->d.precision == 64 ? 8.0 : 4.0;
     // algorithmic bytes per launch: every state word read once and written once
     const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);

@@ -1,4 +1,6 @@
 // Launch wrappers and helper kernels; explicit FP32 / FP64 instantiations.
+#include <utility>
+
 #include "fdtd_kernels.cuh"
 #include "fdtd_launch.h"
 #include "fdtd_shell2.cuh"
@@ -84,6 +86,25 @@ __global__ void index_map_kernel(const KParams<T> p, int which, int32_t* out)
 
 static dim3 grid3(int nx, int ny, int nz) { return dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY, nz); }
 
+// Launch of a kernel of the step chain; pdl: as a programmatic dependent launch (its blocks may start
+// before the kernel before it in the stream has completed; see pdl_wait / pdl_trigger).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_chain(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, bool pdl,
+                                Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 int pole_bucket(int max_poles)
 {
     return max_poles == 0 ? 0 : max_poles <= 4 ? 4 : max_poles <= 8 ? 8 : 16;
@@ -95,12 +116,74 @@ cudaError_t prepare_step()
     return cudaFuncSetAttribute(step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StepSmem<T>::total);
 }
 
+// A kernel node of a step graph (no dependencies yet; the host adds them).
+template <typename... KArgs, typename... Args>
+static cudaError_t graph_kernel(cudaGraph_t g, cudaGraphNode_t* node, void (*k)(KArgs...), dim3 grid, dim3 block,
+                                size_t smem, Args... args)
+{
+    void* ptrs[] = {(void*)&args...};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = ptrs;
+    return cudaGraphAddKernelNode(node, g, nullptr, 0, &kp);
+}
+
 template <typename T>
-cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s)
+cudaError_t graph_step(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const StepMaps& m)
+{
+    const dim3 grid((p.ib[1] - p.ib[0]) / kTX, (p.ib[3] - p.ib[2]) / kTY, (p.ib[5] - p.ib[4] + kKC - 1) / kKC);
+    return graph_kernel(g, node, step_kernel<T>, grid, dim3(kPX, kTY), StepSmem<T>::total, p, m);
+}
+
+template <typename T>
+cudaError_t graph_shell(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const ShellBoxes& s, bool e_part)
+{
+    const dim3 grid(s.first[s.n]), b(kBX, kBY);
+    if constexpr (sizeof(T) == 4) {
+        if (s.pair)
+            return e_part ? graph_kernel(g, node, shell_e2_kernel, grid, b, 0, p, s)
+                          : graph_kernel(g, node, shell_h2_kernel, grid, b, 0, p, s);
+    }
+    return e_part ? graph_kernel(g, node, shell_e_kernel<T>, grid, b, 0, p, s)
+                  : graph_kernel(g, node, shell_h_kernel<T>, grid, b, 0, p, s);
+}
+
+template <typename T>
+cudaError_t graph_e_design(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const PoleTable<T>& tab, int bucket)
+{
+    const dim3 b(kBX, kBY);
+    const dim3 g3 = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
+    const dim3 grid(g3.x, g3.y, 3 * ((g3.z + p.edz - 1) / p.edz));
+    switch (bucket) {
+    case 0: return graph_kernel(g, node, e_design_kernel<T, 0>, grid, b, 0, p, tab);
+    case 4: return graph_kernel(g, node, e_design_kernel<T, 4>, grid, b, 0, p, tab);
+    case 8: return graph_kernel(g, node, e_design_kernel<T, 8>, grid, b, 0, p, tab);
+    default: return graph_kernel(g, node, e_design_kernel<T, 16>, grid, b, 0, p, tab);
+    }
+}
+
+template <typename T>
+cudaError_t graph_dft(cudaGraph_t g, cudaGraphNode_t* node, const DParams<T>& d, int cnt)
+{
+    return graph_kernel(g, node, dft_kernel<T>, dim3((unsigned)((d.nd + kReduceThreads - 1) / kReduceThreads)),
+                        dim3(kReduceThreads), 0, d, cnt);
+}
+
+template <typename T>
+unsigned step_blocks(const KParams<T>& p)
+{
+    return (unsigned)((p.ib[1] - p.ib[0]) / kTX) * (unsigned)((p.ib[3] - p.ib[2]) / kTY) *
+           (unsigned)((p.ib[5] - p.ib[4] + kKC - 1) / kKC);
+}
+
+template <typename T>
+cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s, bool pdl)
 {
     const dim3 g((p.ib[1] - p.ib[0]) / kTX, (p.ib[3] - p.ib[2]) / kTY, (p.ib[5] - p.ib[4] + kKC - 1) / kKC);
-    step_kernel<T><<<g, dim3(kPX, kTY), StepSmem<T>::total, s>>>(p, m);
-    return cudaGetLastError();
+    return launch_chain(step_kernel<T>, g, dim3(kPX, kTY), StepSmem<T>::total, s, pdl, p, m);
 }
 
 // Launches with fewer blocks than this (two per SM) get shorter per-thread columns, so that small
@@ -127,48 +210,41 @@ unsigned shell_blocks(ShellBoxes& s)
 }
 
 template <typename T>
-cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, cudaStream_t st)
+cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, cudaStream_t st, bool pdl)
 {
     const unsigned nb = s.first[s.n];
     if (nb == 0) return cudaSuccess;
+    const dim3 b(kBX, kBY);
     if constexpr (sizeof(T) == 4) {
-        if (s.pair) {
-            if (e_part)
-                shell_e2_kernel<<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
-            else
-                shell_h2_kernel<<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
-            return cudaGetLastError();
-        }
+        if (s.pair)
+            return e_part ? launch_chain(shell_e2_kernel, dim3(nb), b, 0, st, pdl, p, s)
+                          : launch_chain(shell_h2_kernel, dim3(nb), b, 0, st, pdl, p, s);
     }
-    if (e_part)
-        shell_e_kernel<T><<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
-    else
-        shell_h_kernel<T><<<nb, dim3(kBX, kBY), 0, st>>>(p, s);
-    return cudaGetLastError();
+    return e_part ? launch_chain(shell_e_kernel<T>, dim3(nb), b, 0, st, pdl, p, s)
+                  : launch_chain(shell_h_kernel<T>, dim3(nb), b, 0, st, pdl, p, s);
 }
 
 template <typename T>
-cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bucket, cudaStream_t s)
+cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bucket, cudaStream_t s, bool pdl)
 {
     if (p.nd == 0) return cudaSuccess;
     const dim3 b(kBX, kBY);
     const dim3 g3 = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
     const dim3 g(g3.x, g3.y, 3 * ((g3.z + p.edz - 1) / p.edz));   // one block per (p.edz planes, component)
     switch (bucket) {
-    case 0: e_design_kernel<T, 0><<<g, b, 0, s>>>(p, tab); break;
-    case 4: e_design_kernel<T, 4><<<g, b, 0, s>>>(p, tab); break;
-    case 8: e_design_kernel<T, 8><<<g, b, 0, s>>>(p, tab); break;
-    default: e_design_kernel<T, 16><<<g, b, 0, s>>>(p, tab); break;
+    case 0: return launch_chain(e_design_kernel<T, 0>, g, b, 0, s, pdl, p, tab);
+    case 4: return launch_chain(e_design_kernel<T, 4>, g, b, 0, s, pdl, p, tab);
+    case 8: return launch_chain(e_design_kernel<T, 8>, g, b, 0, s, pdl, p, tab);
+    default: return launch_chain(e_design_kernel<T, 16>, g, b, 0, s, pdl, p, tab);
     }
-    return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s)
+cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s, bool pdl)
 {
     if (d.nd == 0 || cnt <= 0) return cudaSuccess;
-    dft_kernel<T><<<(unsigned)((d.nd + kReduceThreads - 1) / kReduceThreads), kReduceThreads, 0, s>>>(d, cnt);
-    return cudaGetLastError();
+    return launch_chain(dft_kernel<T>, dim3((unsigned)((d.nd + kReduceThreads - 1) / kReduceThreads)),
+                        dim3(kReduceThreads), 0, s, pdl, d, cnt);
 }
 
 
@@ -271,10 +347,15 @@ cudaError_t launch_rho_scatter(const void* src, int dtype, long long n, const lo
 
 #define FDTD_INSTANTIATE(T)                                                                              \
     template cudaError_t prepare_step<T>();                                                              \
-    template cudaError_t launch_step<T>(const KParams<T>&, const StepMaps&, cudaStream_t);               \
-    template cudaError_t launch_shell<T>(const KParams<T>&, const ShellBoxes&, bool, cudaStream_t);      \
-    template cudaError_t launch_e_design<T>(const KParams<T>&, const PoleTable<T>&, int, cudaStream_t);                       \
-    template cudaError_t launch_dft<T>(const DParams<T>&, int, cudaStream_t);                            \
+    template unsigned step_blocks<T>(const KParams<T>&);                                                \
+    template cudaError_t graph_step<T>(cudaGraph_t, cudaGraphNode_t*, const KParams<T>&, const StepMaps&); \
+    template cudaError_t graph_shell<T>(cudaGraph_t, cudaGraphNode_t*, const KParams<T>&, const ShellBoxes&, bool); \
+    template cudaError_t graph_e_design<T>(cudaGraph_t, cudaGraphNode_t*, const KParams<T>&, const PoleTable<T>&, int); \
+    template cudaError_t graph_dft<T>(cudaGraph_t, cudaGraphNode_t*, const DParams<T>&, int);           \
+    template cudaError_t launch_step<T>(const KParams<T>&, const StepMaps&, cudaStream_t, bool);         \
+    template cudaError_t launch_shell<T>(const KParams<T>&, const ShellBoxes&, bool, cudaStream_t, bool); \
+    template cudaError_t launch_e_design<T>(const KParams<T>&, const PoleTable<T>&, int, cudaStream_t, bool); \
+    template cudaError_t launch_dft<T>(const DParams<T>&, int, cudaStream_t, bool);                      \
     template cudaError_t launch_grad<T>(const GParams<T>&, unsigned, cudaStream_t);                      \
     template cudaError_t launch_rho_import<T>(const void*, int, long long, T*, int*, cudaStream_t);      \
     template cudaError_t launch_rho_scatter<T>(const void*, int, long long, const long long*, const int (*)[3], int, \

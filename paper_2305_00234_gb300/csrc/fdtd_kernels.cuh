@@ -193,6 +193,15 @@ __device__ __forceinline__ T point_drive(const KParams<T>& p, int i, int j, int 
 template <typename T>
 __device__ __forceinline__ int read_step(const int* ctl) { return __ldcg(ctl); }
 
+// Programmatic dependent launch.  In the step graphs the kernels of a phase depend on those of the phase
+// before through programmatic edges: a kernel's blocks may be launched before its predecessors have
+// finished; pdl_wait() blocks until every predecessor has completed and its memory is visible, and
+// pdl_trigger() lets the successors' blocks be launched once every block of this kernel has issued it.
+// Every kernel of the step graphs waits first and triggers right after, so the next phase's blocks are
+// already resident when a phase drains.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // The last block of the launch that owns the step advance moves the device step counter on.
 __device__ __forceinline__ void finish_step(int* ctl, unsigned nblocks, int n)
 {
@@ -303,6 +312,8 @@ __global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_ke
     const int i = p.db[0] + blockIdx.x * kBX + threadIdx.x;
     const int j = p.db[2] + blockIdx.y * kBY + threadIdx.y;
     const int k0 = p.db[4] + zc * p.edz, k1 = min(p.db[5], k0 + p.edz);
+    pdl_wait();
+    pdl_trigger();
     const int n = read_step<T>(p.ctl);
     if (i < p.db[1] && j < p.db[3]) {
         const T emax = c == 0 ? e_design_column<T, MP, 0>(p, tab, i, j, k0, k1, n)
@@ -360,6 +371,8 @@ __device__ __forceinline__ void dft_voxel(const DParams<T>& d, long long v, int 
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) dft_kernel(const DParams<T> d, int cnt)
 {
+    pdl_wait();                                   // the snapshots of the block's last step
+    pdl_trigger();
     const long long v = (long long)blockIdx.x * kReduceThreads + threadIdx.x;
     if (v >= d.nd) return;
     dft_voxel<T, false>(d, v, __ldcg(d.ctl) - cnt, cnt);

@@ -10,15 +10,27 @@ namespace fdtd {
 int pole_bucket(int max_poles);
 template <typename T>
 cudaError_t prepare_step();
+// pdl: launch as a programmatic dependent launch in the step chain (see pdl_wait in fdtd_kernels.cuh)
 template <typename T>
-cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s);
+unsigned step_blocks(const KParams<T>& p);
+// kernel nodes of a step graph, without dependencies
 template <typename T>
-cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bucket, cudaStream_t s);
+cudaError_t graph_step(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const StepMaps& m);
 template <typename T>
-cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s);
+cudaError_t graph_shell(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const ShellBoxes& s, bool e_part);
+template <typename T>
+cudaError_t graph_e_design(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const PoleTable<T>& tab, int bucket);
+template <typename T>
+cudaError_t graph_dft(cudaGraph_t g, cudaGraphNode_t* node, const DParams<T>& d, int cnt);
+template <typename T>
+cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s, bool pdl = false);
+template <typename T>
+cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bucket, cudaStream_t s, bool pdl = false);
+template <typename T>
+cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s, bool pdl = false);
 unsigned shell_blocks(ShellBoxes& s);   // fills s.first, returns the launch's blocks
 template <typename T>
-cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, cudaStream_t st);
+cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, cudaStream_t st, bool pdl = false);
 unsigned design_blocks(int dnx, int dny, int dnz, int& edz);   // also picks the column depth
 template <typename T>
 cudaError_t launch_grad(const GParams<T>& g, unsigned nblocks, cudaStream_t s);

@@ -105,6 +105,8 @@ __device__ __forceinline__ void psi_store_p(float* const (&ps)[3][2], const PsiC
 __global__ void __launch_bounds__(kBX * kBY, FDTD_SHELL2_MINB) shell_h2_kernel(const KParams<float> p, const ShellBoxes s)
 {
     constexpr int P = kShell2PZ;
+    pdl_wait();
+    pdl_trigger();
     ShellCol cl;
     if (!shell_pair(s, cl)) return;
     const int x = cl.x, y = cl.y;
@@ -201,6 +203,8 @@ __global__ void __launch_bounds__(kBX * kBY, FDTD_SHELL2_MINB) shell_h2_kernel(c
 __global__ void __launch_bounds__(kBX * kBY, FDTD_SHELL2_MINB) shell_e2_kernel(const KParams<float> p, const ShellBoxes s)
 {
     constexpr int P = kShell2PZ;
+    pdl_wait();
+    pdl_trigger();
     ShellCol cl;
     const bool live = shell_pair(s, cl);
     const int n = read_step<float>(p.ctl);

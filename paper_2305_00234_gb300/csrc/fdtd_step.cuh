@@ -354,6 +354,8 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
     const int k_first = kb - 1;            // >= 0: the interior box starts above plane 0
     const int ne_tot = ke - k_first + 1;   // E planes k_first .. ke
     const int nh_tot = ke - k_first;       // H planes k_first .. ke-1
+    pdl_wait();
+    pdl_trigger();
     const int n = read_step<T>(p.ctl);
     auto eslot = [&](int s) { return (T*)((unsigned char*)sE + s * S::e_slot); };
     auto hslot = [&](int s) { return (T*)((unsigned char*)sHo + s * S::h_slot); };
@@ -657,9 +659,10 @@ __device__ __forceinline__ void h_column(const KParams<T>& p, int x, int y, int 
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_h_kernel(const KParams<T> p, const ShellBoxes s)
 {
+    pdl_wait();
+    pdl_trigger();
     ShellCol cl;
-    if (!shell_cell(s, cl)) return;
-    h_column<T, false>(p, cl.x, cl.y, cl.k0, cl.k1, read_step<T>(p.ctl));
+    if (shell_cell(s, cl)) h_column<T, false>(p, cl.x, cl.y, cl.k0, cl.k1, read_step<T>(p.ctl));
 }
 
 // E^{n+1} of the cells of one column (x, y), planes [k0, k1), that lie outside the working box, from
@@ -773,6 +776,8 @@ __device__ __forceinline__ T e_column(const KParams<T>& p, int x, int y, int k0,
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY, sizeof(T) == 8 ? 2 : FDTD_SHELL_MINB) shell_e_kernel(const KParams<T> p, const ShellBoxes s)
 {
+    pdl_wait();
+    pdl_trigger();
     ShellCol cl;
     const bool live = shell_cell(s, cl);
     const int n = read_step<T>(p.ctl);

@@ -113,7 +113,9 @@ def test_step_paths(gpu, prec, nx, fused, src):
     rho = synth.smooth_rho(synth.box_shape(d["design_box"]), 23, 2.0)
     w = dict(desc=d, bg=vacuum(), m1=vacuum(), m2=synth.drude_lorentz_metal(23, 3), gamma=1e6, rho=rho)
     g = run_gpu(gpu, w)
-    assert g["p"].timings()["fused_step"] == fused
+    t = g["p"].timings()
+    assert t["fused_step"] == fused
+    assert t["pdl_graphs"] == 1                    # phases linked by programmatic dependent launch edges
     compare(g, run_oracle(w), prec)
 
 
