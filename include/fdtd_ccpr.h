@@ -138,6 +138,9 @@ typedef struct {
                                                 x bound of the grid, the x CPML and the shell boxes even) */
     long long pdl_graphs;                    /* 1: the step graphs link each phase to the next through
                                                 programmatic dependent launch edges; 0: ordinary edges */
+    long long paired_design;                 /* 1: the design-E kernel updates x-adjacent sample pairs (FP32,
+                                                up to 8 poles a component, nx and the working box's x origin
+                                                and extent even) */
 } fdtd_timings;
 
 /* Create a problem on the given CUDA stream (cudaStream_t; NULL = default stream) of the current

@@ -58,7 +58,7 @@ class Timings(C.Structure):
                                           "bytes_shell_e_per_launch", "bytes_ed_per_launch", "bytes_dft_per_launch",
                                           "bytes_grad_per_launch", "dft_steps_per_launch")] + \
                [("fused_step", C.c_longlong), ("interior_cells", C.c_double), ("interior_design_cells", C.c_double),
-                ("paired_shell", C.c_longlong), ("pdl_graphs", C.c_longlong)]
+                ("paired_shell", C.c_longlong), ("pdl_graphs", C.c_longlong), ("paired_design", C.c_longlong)]
 
 
 class FdtdError(RuntimeError):

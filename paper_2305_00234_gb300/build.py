@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libfdtdccpr.so")
 SOURCES = ["fdtd_api.cu", "fdtd_kernels.cu", "fdtd_batch.cu", "fdtd_noalloc.cu", "fdtd_filter.cu"]
-HEADERS = ["fdtd_kernels.cuh", "fdtd_step.cuh", "fdtd_launch.h", "fdtd_params.h"]
+HEADERS = ["fdtd_kernels.cuh", "fdtd_step.cuh", "fdtd_shell2.cuh", "fdtd_design2.cuh", "fdtd_launch.h", "fdtd_params.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

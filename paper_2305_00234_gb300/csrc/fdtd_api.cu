@@ -316,6 +316,7 @@ struct SolverBase {
     virtual bool has_interior() const = 0;
     virtual bool paired_shell() const = 0;
     virtual bool pdl_graphs() const = 0;
+    virtual bool paired_design() const = 0;
 };
 
 struct fdtd_ctx {
@@ -395,6 +396,7 @@ struct Solver : SolverBase {
     int ptot[3] = {0, 0, 0};
     bool fused = false;             // an interior box for the fused TMA step kernel exists
     bool use_pdl = true;            // step graphs with programmatic edges between phases (else captured)
+    bool pdl_built = false;         // a step graph with programmatic edges has been instantiated
     StepMaps maps[2]{};             // tensor maps of the buffers read by even / odd steps
     fdtd::ShellBoxes shell{};       // the cells around the interior box
     std::vector<double2> ab_host;
@@ -406,7 +408,8 @@ struct Solver : SolverBase {
     void interior_box(int ib[6]) const override { std::copy(base.ib, base.ib + 6, ib); }
     bool has_interior() const override { return fused; }
     bool paired_shell() const override { return shell.pair != 0; }
-    bool pdl_graphs() const override { return use_pdl && graph[0][0] != nullptr; }
+    bool pdl_graphs() const override { return use_pdl && pdl_built; }
+    bool paired_design() const override { return base.ed_pair != 0; }
     ~Solver() override
     {
         for (auto& g : graph)
@@ -547,7 +550,8 @@ struct Solver : SolverBase {
         shell.pair = shell_pairable(p) ? 1 : 0;
         p.nblocks_s = fdtd::shell_blocks(shell);
         p.edz = 1;
-        p.nblocks_d = c->nd ? fdtd::design_blocks(c->dn[0], c->dn[1], c->dn[2], p.edz) : 0;
+        p.ed_pair = design_pairable() ? 1 : 0;
+        p.nblocks_d = c->nd ? fdtd::design_blocks(p.ed_pair ? c->dn[0] / 2 : c->dn[0], c->dn[1], c->dn[2], p.edz) : 0;
         p.nblocks_e = p.nblocks_s + p.nblocks_d;
         p.blowup = (T)1e30;
         p.n_steps = d.n_steps;
@@ -789,6 +793,21 @@ struct Solver : SolverBase {
         for (int q = 0; q < shell.n; ++q)
             if (shell.b[q][0] % 2 || shell.b[q][1] % 2) return false;
         return true;
+    }
+
+    // The paired design-E kernel (FP32) needs nx and the working box's x origin and extent even (a pair's
+    // samples adjacent and 8-byte aligned in the fields, densities, snapshots and pole currents), and up
+    // to 8 poles a component (more would spill the pair's pole currents).
+    // FDTD_ED_PAIR 0 (build knob) keeps the one-sample kernel.
+    bool design_pairable() const
+    {
+#if defined(FDTD_ED_PAIR) && !FDTD_ED_PAIR
+        return false;
+#else
+        const fdtd_grid_desc& d = c->d;
+        return sizeof(T) == 4 && c->nd && bucket <= 8 && d.nx % 2 == 0 && d.design_box[0] % 2 == 0 &&
+               c->dn[0] % 2 == 0;
+#endif
     }
 
     // Background part of one step: H of the shell and the fused interior (both read only the old
@@ -1259,6 +1278,7 @@ struct Solver : SolverBase {
         if (use_pdl) {
             if (cudaGraphExec_t ex = build_pdl_graph(mode, steps)) {
                 graph[mode][which] = ex;
+                pdl_built = true;
                 return;
             }
             use_pdl = false;    // the driver refused the programmatic edges: captured graphs from here on
@@ -2417,6 +2437,7 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     t.fused_step = h->impl && h->impl->has_interior() ? 1 : 0;
     t.paired_shell = h->impl && h->impl->paired_shell() ? 1 : 0;
     t.pdl_graphs = h->impl && h->impl->pdl_graphs() ? 1 : 0;
+    t.paired_design = h->impl && h->impl->paired_design() ? 1 : 0;
     const double ts = h->d.precision == 64 ? 8.0 : 4.0;
     // algorithmic bytes per launch: every state word read once and written once
     const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);

@@ -1,6 +1,7 @@
 // Launch wrappers and helper kernels; explicit FP32 / FP64 instantiations.
 #include <utility>
 
+#include "fdtd_design2.cuh"
 #include "fdtd_kernels.cuh"
 #include "fdtd_launch.h"
 #include "fdtd_shell2.cuh"
@@ -151,12 +152,27 @@ cudaError_t graph_shell(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& 
                   : graph_kernel(g, node, shell_h_kernel<T>, grid, b, 0, p, s);
 }
 
+// Grid of the design-E kernel: one block per (p.edz planes, component) of 32 x 8 columns (32 x 8 column
+// pairs for the paired kernel).
+template <typename T>
+static dim3 design_grid(const KParams<T>& p)
+{
+    const dim3 g3 = grid3((p.db[1] - p.db[0]) / (p.ed_pair ? 2 : 1), p.db[3] - p.db[2], p.db[5] - p.db[4]);
+    return dim3(g3.x, g3.y, 3 * ((g3.z + p.edz - 1) / p.edz));
+}
+
 template <typename T>
 cudaError_t graph_e_design(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const PoleTable<T>& tab, int bucket)
 {
-    const dim3 b(kBX, kBY);
-    const dim3 g3 = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
-    const dim3 grid(g3.x, g3.y, 3 * ((g3.z + p.edz - 1) / p.edz));
+    const dim3 b(kBX, kBY), grid = design_grid(p);
+    if constexpr (sizeof(T) == 4) {
+        if (p.ed_pair) switch (bucket) {
+            case 0: return graph_kernel(g, node, e_design2_kernel<0>, grid, b, 0, p, tab);
+            case 4: return graph_kernel(g, node, e_design2_kernel<4>, grid, b, 0, p, tab);
+            case 8: return graph_kernel(g, node, e_design2_kernel<8>, grid, b, 0, p, tab);
+            default: return cudaErrorInvalidValue;   // the host pairs only up to 8 poles a component
+            }
+    }
     switch (bucket) {
     case 0: return graph_kernel(g, node, e_design_kernel<T, 0>, grid, b, 0, p, tab);
     case 4: return graph_kernel(g, node, e_design_kernel<T, 4>, grid, b, 0, p, tab);
@@ -228,9 +244,15 @@ template <typename T>
 cudaError_t launch_e_design(const KParams<T>& p, const PoleTable<T>& tab, int bucket, cudaStream_t s, bool pdl)
 {
     if (p.nd == 0) return cudaSuccess;
-    const dim3 b(kBX, kBY);
-    const dim3 g3 = grid3(p.db[1] - p.db[0], p.db[3] - p.db[2], p.db[5] - p.db[4]);
-    const dim3 g(g3.x, g3.y, 3 * ((g3.z + p.edz - 1) / p.edz));   // one block per (p.edz planes, component)
+    const dim3 b(kBX, kBY), g = design_grid(p);
+    if constexpr (sizeof(T) == 4) {
+        if (p.ed_pair) switch (bucket) {
+            case 0: return launch_chain(e_design2_kernel<0>, g, b, 0, s, pdl, p, tab);
+            case 4: return launch_chain(e_design2_kernel<4>, g, b, 0, s, pdl, p, tab);
+            case 8: return launch_chain(e_design2_kernel<8>, g, b, 0, s, pdl, p, tab);
+            default: return cudaErrorInvalidValue;   // the host pairs only up to 8 poles a component
+            }
+    }
     switch (bucket) {
     case 0: return launch_chain(e_design_kernel<T, 0>, g, b, 0, s, pdl, p, tab);
     case 4: return launch_chain(e_design_kernel<T, 4>, g, b, 0, s, pdl, p, tab);

@@ -344,7 +344,43 @@ def test_paired_shell_paths(gpu, src):
     g = run_gpu(gpu, w)
     t = g["p"].timings()
     assert t["fused_step"] == 1 and t["paired_shell"] == 1
+    assert t["paired_design"] == 0                 # odd working-box x origin: the one-sample design kernel
     compare(g, run_oracle(w), 32, per_voxel=per_voxel)
+
+
+@pytest.mark.parametrize("case", ["gap_odd", "gap_even", "tfsf_in_design_odd", "tfsf_in_design_even",
+                                  "poles8", "no_poles", "per_sample"])
+def test_paired_design_paths(gpu, case):
+    """The paired FP32 design-E kernel (two x-adjacent samples per thread): an even grid with the design
+    box's x origin and extent even; the gap box (the adjoint run's sources) and the forward dipole on
+    either sample of a pair, the TF/SF plane through the design box on either sample of a pair, 6 and
+    0 poles a component, and the per-sample density layout (working box grown by one on +x, E_x samples
+    of its last x column outside their sample box)."""
+    gap = (4, 2, 2) if case == "gap_even" else (2, 2, 2)
+    kw = {"gap_odd": dict(src_kind=0, src_comp=2, src_pos=(27, 21, 18)),
+          "gap_even": dict(src_kind=0, src_comp=0, src_pos=(25, 21, 18)),
+          "tfsf_in_design_odd": dict(src_kind=1, src_pos=(23, 0, 0)),
+          "tfsf_in_design_even": dict(src_kind=1, src_pos=(30, 0, 0))}.get(case, dict(src_kind=1, src_pos=(9, 0, 0)))
+    design = (23, 18, 15) if case == "per_sample" else (24, 18, 15)
+    d = base_desc(56, 42, 37, n_steps=420, cpml=(6, 4, 4, 7, 5, 3), precision=32,
+                  design=design, gap=gap, lambdas_nm=(500.0, 650.0), **kw)
+    rho = synth.smooth_rho(synth.box_shape(d["design_box"]), 41, 2.0)
+    m1, m2 = vacuum(), synth.drude_lorentz_metal(41, 3)
+    if case == "poles8":
+        m1 = synth.lorentz_dielectric(42, 2, eps_inf=(11.7, 11.7, 12.1))
+        m2 = synth.drude_lorentz_metal(41, 4)
+    if case == "no_poles":
+        m2 = dict(vacuum(), eps_inf=[4.0, 4.5, 5.0], sigma=[2e5, 2e5, 2e5])
+    w = dict(desc=d, bg=vacuum(), m1=m1, m2=m2, gamma=1e6, rho=rho)
+    if case == "per_sample":
+        w = per_sample(w, 43)
+    db, gb = w["desc"]["design_box"], w["desc"]["gap_box"]
+    assert db[0] % 2 == 0 and (db[1] - db[0] + (case == "per_sample")) % 2 == 0
+    assert gb[0] % 2 == (case != "gap_even")
+    g = run_gpu(gpu, w)
+    t = g["p"].timings()
+    assert t["paired_design"] == 1 and t["fused_step"] == 1
+    compare(g, run_oracle(w), 32, per_voxel=case != "per_sample")
 
 
 def per_sample(w, seed):
