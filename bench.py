@@ -623,7 +623,9 @@ def run_ours(args):
     # written once).  They differ only for the interior kernel (48 B per cell against 72 B) and the
     # design-E kernel (its E snapshot for the blocked DFT is not a term of the method).
     ts = 4.0 if d["precision"] == 32 else 8.0
-    method = {"step": 9.0 * ts * (2.0 * tim["interior_cells"] - tim["interior_design_cells"]),
+    ni, ndi = tim["interior_cells"], tim["interior_design_cells"]
+    psi_in = tim["bytes_step_per_launch"] - ts * (12.0 * ni - 3.0 * ndi)   # psi of the slab cells it updates
+    method = {"step": 9.0 * ts * (2.0 * ni - ndi) + psi_in,
               "ed": tim["bytes_ed_per_launch"] - 3.0 * ts * p.nd}
     for k in ("shell_h", "step", "shell_e", "ed", "dft", "grad"):
         nl = tim[f"{k}_launches"]

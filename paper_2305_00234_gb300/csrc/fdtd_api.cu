@@ -1229,6 +1229,7 @@ struct Solver : SolverBase {
             cudaGetLastError();
             return nullptr;
         }
+        const bool has_shell = shell.first[shell.n] > 0;   // the fused kernel may cover the whole grid
         cudaGraphEdgeData ed = {};
         ed.type = cudaGraphDependencyTypeProgrammatic;
         ed.from_port = cudaGraphKernelNodePortProgrammatic;
@@ -1248,12 +1249,14 @@ struct Solver : SolverBase {
             const KParams<T> q = par(p, st);
             phase([&] {
                 cudaGraphNode_t n = nullptr;
-                if (e == cudaSuccess && (e = fdtd::graph_shell<T>(g, &n, q, shell, false)) == cudaSuccess) cur.push_back(n);
+                if (e == cudaSuccess && has_shell && (e = fdtd::graph_shell<T>(g, &n, q, shell, false)) == cudaSuccess)
+                    cur.push_back(n);
                 if (e == cudaSuccess && fused && (e = fdtd::graph_step<T>(g, &n, q, maps[st & 1])) == cudaSuccess) cur.push_back(n);
             });
             phase([&] {
                 cudaGraphNode_t n = nullptr;
-                if (e == cudaSuccess && (e = fdtd::graph_shell<T>(g, &n, q, shell, true)) == cudaSuccess) cur.push_back(n);
+                if (e == cudaSuccess && has_shell && (e = fdtd::graph_shell<T>(g, &n, q, shell, true)) == cudaSuccess)
+                    cur.push_back(n);
                 if (e == cudaSuccess && c->nd && (e = fdtd::graph_e_design<T>(g, &n, q, htab, bucket)) == cudaSuccess)
                     cur.push_back(n);
             });
@@ -2443,29 +2446,35 @@ fdtd_status fdtd_get_timings(fdtd_handle h, fdtd_timings* out)
     const double nc = (double)h->ncell, nd = (double)h->nd, nod = (double)(h->nd - h->ngap);
     // interior (fused) kernel: E^n and H read, H written, E written outside the design box;
     // shell kernels: H: E^n, H read, H written; E: H, E^n read, E written (outside the design box);
-    // psi: per CPML slab cell and axis two psi_H read and written (H kernel), two psi_E (E kernel)
+    // psi: per CPML slab cell and axis two psi_H read and written (H update), two psi_E (E update), in
+    // the kernel that owns the cell
     double bst = 0.0, bsh = 0.0, bse = 0.0;
+    const int n[3] = {h->d.nx, h->d.ny, h->d.nz};
+    int ib[6] = {0, 0, 0, 0, 0, 0};
+    if (h->impl) h->impl->interior_box(ib);
+    for (int a = 0; a < 3; ++a) {
+        const int lo = h->d.cpml[2 * a], hi = h->d.cpml[2 * a + 1];
+        const double slab = (double)h->ncell / n[a] * (lo + hi);
+        double in = (double)(std::max(0, std::min(ib[2 * a + 1], lo) - ib[2 * a]) +
+                             std::max(0, ib[2 * a + 1] - std::max(ib[2 * a], n[a] - hi)));
+        for (int b = 0; b < 3; ++b)
+            if (b != a) in *= ib[2 * b + 1] - ib[2 * b];
+        bst += 8.0 * ts * in;
+        bsh += 4.0 * ts * (slab - in);
+        bse += 4.0 * ts * (slab - in);
+    }
     if (h->impl) {
-        int ib[6];
-        h->impl->interior_box(ib);
         const double ni = (double)(ib[1] - ib[0]) * (ib[3] - ib[2]) * (ib[5] - ib[4]);
         const int* db = h->d.design_box;
         double ndi = 1.0;
         for (int a = 0; a < 3; ++a)
             ndi *= std::max(0, std::min(ib[2 * a + 1], db[2 * a + 1]) - std::max(ib[2 * a], db[2 * a]));
         if (box_count(db) == 0) ndi = 0.0;
-        bst = 12.0 * ts * ni - 3.0 * ts * ndi;
+        bst += 12.0 * ts * ni - 3.0 * ts * ndi;
         t.interior_cells = ni;
         t.interior_design_cells = ndi;
-        bsh = 9.0 * ts * (nc - ni);
-        bse = 9.0 * ts * ((nc - ni) - (nd - ndi));
-    }
-    const int n[3] = {h->d.nx, h->d.ny, h->d.nz};
-    for (int a = 0; a < 3; ++a) {
-        const double w = (double)h->d.cpml[2 * a] + h->d.cpml[2 * a + 1];
-        const double slab = nc / n[a] * w;
-        bsh += 4.0 * ts * slab;
-        bse += 4.0 * ts * slab;
+        bsh += 9.0 * ts * (nc - ni);
+        bse += 9.0 * ts * ((nc - ni) - (nd - ndi));
     }
     double bd = 9.0 * ts * nd;                          // inside the design box: E^n, H^{n+1/2} read, E written
     if (h->impl) {
