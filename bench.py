@@ -252,7 +252,7 @@ def kernel_hash():
     """Hash of the device-kernel sources with comments and whitespace removed (a comment edit does not
     change the kernels the DRAM counters were taken on)."""
     h = hashlib.sha256()
-    for f in ("fdtd_kernels.cuh", "fdtd_step.cuh", "fdtd_params.h"):
+    for f in ("fdtd_kernels.cuh", "fdtd_step.cuh", "fdtd_shell2.cuh", "fdtd_design2.cuh", "fdtd_params.h"):
         with open(os.path.join(ROOT, "paper_2305_00234_gb300", "csrc", f), "rb") as fh:
             t = fh.read().decode()
         t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
@@ -606,8 +606,10 @@ def run_ours(args):
     # on the library's stream over the timed region); the dominant kernel is the one with most time
     peak, peak_src = measured_peaks()
     prec_t = "float" if d["precision"] == 32 else "double"
-    names = {"shell_h": f"shell_h_kernel<{prec_t}>", "step": f"step_kernel<{prec_t}>",
-             "shell_e": f"shell_e_kernel<{prec_t}>", "ed": f"e_design_kernel<{prec_t},*>",
+    names = {"shell_h": "shell_h2_kernel" if tim["paired_shell"] else f"shell_h_kernel<{prec_t}>",
+             "step": f"step_kernel<{prec_t}>",
+             "shell_e": "shell_e2_kernel" if tim["paired_shell"] else f"shell_e_kernel<{prec_t}>",
+             "ed": "e_design2_kernel<*>" if tim["paired_design"] else f"e_design_kernel<{prec_t},*>",
              "dft": f"dft_kernel<{prec_t}>", "grad": f"grad_kernel<{prec_t}>"}
     kern = {}
     runs = 2 * args.steps                                   # forward + adjoint per gradient in the timed region

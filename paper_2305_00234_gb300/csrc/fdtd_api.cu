@@ -756,6 +756,9 @@ struct Solver : SolverBase {
     // cpml_z_low + 1 .. nz - cpml_z_high - 1 (the plane below the first one is outside the slab too).
     // Needs x rows of a multiple of 16 bytes and the tensor-map encoder.  The rest of the grid is the
     // shell: at most six boxes.
+#ifndef FDTD_STEP_MINBLK
+#define FDTD_STEP_MINBLK (2 * 152)
+#endif
     void split_grid(KParams<T>& p)
     {
         const fdtd_grid_desc& d = c->d;
@@ -766,6 +769,10 @@ struct Solver : SolverBase {
         const int ib[6] = {X0, X0 + ntx * fdtd::kTX, Y0, Y0 + nty * fdtd::kTY, Z0, Z1};
         std::fill(p.ib, p.ib + 6, 0);
         if (fused) std::copy(ib, ib + 6, p.ib);
+        // z planes per block: kKC, halved while the launch has fewer than FDTD_STEP_MINBLK blocks
+        p.kc = fdtd::kKC;
+        if (fused)
+            while (p.kc > 2 && (unsigned)ntx * nty * ((Z1 - Z0 + p.kc - 1) / p.kc) < FDTD_STEP_MINBLK) p.kc /= 2;
         shell = fdtd::ShellBoxes{};
         auto add = [&](int x0, int x1, int y0, int y1, int z0, int z1) {
             if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;

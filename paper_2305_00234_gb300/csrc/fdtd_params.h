@@ -164,6 +164,7 @@ struct KParams {
     unsigned nblocks_s;          // blocks of the background-E shell kernel
     unsigned nblocks_d;          // blocks of e_design_kernel
     int edz;                     // z planes per thread of e_design_kernel (<= kEdZ)
+    int kc;                      // z planes per block of step_kernel (<= kKC)
     int ed_pair;                 // 1: e_design2_kernel (FP32, x-adjacent sample pairs; nx and the working box's
                                  // x origin and extent even, one density per voxel)
     unsigned nblocks_e;          // blocks of the E phase (shell E + design E); the last one advances the step

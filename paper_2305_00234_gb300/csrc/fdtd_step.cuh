@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
     const int i0 = p.ib[0] + blockIdx.x * kTX, j0 = p.ib[2] + blockIdx.y * kTY;
     const int i = i0 + 2 * tx, j = j0 + ty;                            // first cell of the own pair
-    const int kb = p.ib[4] + blockIdx.z * kKC, ke = min(kb + kKC, p.ib[5]);
+    const int kb = p.ib[4] + blockIdx.z * p.kc, ke = min(kb + p.kc, p.ib[5]);
     const int k_first = kb - 1;            // >= 0: the interior box starts above plane 0
     const int ne_tot = ke - k_first + 1;   // E planes k_first .. ke
     const int nh_tot = ke - k_first;       // H planes k_first .. ke-1
