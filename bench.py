@@ -53,8 +53,11 @@ def parse(argv=None):
                     help="requests of the same stream replayed again with arrivals slowed to about 0.7 of the "
                          "server's measured capacity (latency below saturation; 0: skip)")
     ap.add_argument("--serving-slots", type=int, default=16)
-    ap.add_argument("--serving-batch-max-cells", type=int, default=64 ** 3,
-                    help="grids of at most this many cells take the batch lane (persistent kernel); -1: all")
+    ap.add_argument("--serving-batch-max-cells", type=int, default=0,
+                    help="grids of at most this many cells take the batch lane (persistent kernel); -1: all; "
+                         "0 (default): none")
+    ap.add_argument("--serving-exclusive-cells", type=int, default=128 ** 3,
+                    help="grids of at least this many cells run one at a time (0: strict FIFO, no limit)")
     ap.add_argument("--precision-study", action="store_true",
                     help="config 3: FP32 fields + FP64 DFT vs all-FP64 build; prints one JSON line")
     ap.add_argument("--filter", action="store_true",
@@ -313,7 +316,8 @@ def cpu_baseline(args, w_full):
 def serving_run(args, device):
     """The seeded serving stream (Poisson, mean 20 req/s; cubic grids 48..192, 1500-4000 steps, 1-4 pole
     pairs): N requests through the continuous-batching server (batch lane: persistent kernel for grids up to
-    --serving-batch-max-cells cells; plain lane: per-request CUDA-graph streams for the others) and, as the
+    --serving-batch-max-cells cells, none by default; plain lane: per-request CUDA-graph streams for the
+    others, grids of --serving-exclusive-cells cells and more one at a time) and, as the
     baseline, the same requests one after another on the same GPU (plain path, FIFO).  The offered load
     (about 2.3e11 cell-updates/s) is above one GPU's capacity, so that replay measures throughput and
     queueing latency; a second replay of the first M requests with arrivals slowed to about 0.7 of the
@@ -325,9 +329,11 @@ def serving_run(args, device):
     from paper_2305_00234_gb300 import serve
     items = synth.serving_stream(n_requests=args.serving_requests)
     bmc = None if args.serving_batch_max_cells < 0 else args.serving_batch_max_cells
+    exc = args.serving_exclusive_cells or None
     cu = sum(2.0 * it["desc"]["nx"] * it["desc"]["ny"] * it["desc"]["nz"] * it["desc"]["n_steps"] for it in items)
     serve.evaluate(serve.from_stream(items[:1])[0])            # warm-up (library, pools)
-    server = serve.GradientServer(max_slots=args.serving_slots, device=device, batch_max_cells=bmc)
+    server = serve.GradientServer(max_slots=args.serving_slots, device=device, batch_max_cells=bmc,
+                                      exclusive_cells=exc)
     res_s, wall_s = serve.replay_stream(serve.from_stream(items), server)
     server.close()
     res_q, wall_q = serve.replay_stream(serve.from_stream(items), None)
@@ -335,6 +341,7 @@ def serving_run(args, device):
     dG = max(float(np.linalg.norm(a.grad - b.grad) / np.linalg.norm(b.grad)) for a, b in zip(res_s, res_q))
     lanes = {ln: sum(1 for r in res_s if r.lane == ln) for ln in ("batch", "plain")}
     out = {"requests": len(items), "rate_hz": 20.0, "slots": args.serving_slots, "batch_max_cells": bmc,
+           "exclusive_cells": exc,
            "server": {"grad_evals_per_s": len(items) / wall_s, "Gcell_updates_per_s": cu / wall_s / 1e9,
                       "wall_s": wall_s, "peak_active": server.peak_active, "peak_batched": server.peak_batched,
                       "batch_launches": server.launches, "lanes": lanes, **serve.latency_stats(res_s)},
@@ -348,7 +355,8 @@ def serving_run(args, device):
         rate = 0.7 * cap
         scale = 20.0 / rate                                        # stretch the 20 req/s arrivals
         sub = items[:m]
-        server = serve.GradientServer(max_slots=args.serving_slots, device=device, batch_max_cells=bmc)
+        server = serve.GradientServer(max_slots=args.serving_slots, device=device, batch_max_cells=bmc,
+                                      exclusive_cells=exc)
         res_l, wall_l = serve.replay_stream(serve.from_stream(sub), server, time_scale=scale)
         server.close()
         out["load_0p7"] = {"requests": m, "offered_rate_hz": rate, "wall_s": wall_l,

@@ -106,6 +106,12 @@ void batch_shape(const fdtd_grid_desc& d, int* sz, int* cw)
     const long long nxy = (long long)d.nx * d.ny;
     *sz = nxy * d.nz >= (1LL << 21) ? 2 * fdtd::kMinBatchSZ : fdtd::kMinBatchSZ;
     *cw = nxy >= 32768 ? 4 * fdtd::kBatchThreads : fdtd::kBatchThreads;
+#ifdef FDTD_BATCH_SZ
+    *sz = FDTD_BATCH_SZ;
+#endif
+#ifdef FDTD_BATCH_CW
+    *cw = FDTD_BATCH_CW;
+#endif
 }
 
 // CFS-CPML coefficients at position u (cells) along an axis of n cells with lo/hi layers.

@@ -189,14 +189,13 @@ __global__ void __launch_bounds__(kBatchThreads, FDTD_BATCH_MINB) batch_kernel(c
             if (ok && kind == 1 && s > 0) ok = wait_count(sl.prog + s - 1, need, L);
             if (ok && L.gate && t == 0) ok = wait_count((const unsigned*)L.gate, 1u, L);   // test hook
             if (!ok && atomicCAS(L.err, 0, 1) == 0) atomicExch(L.err + 1, (int)t);
-            __threadfence();
             s_ok = ok;
-            // the next ticket, taken now so that its round trip overlaps this item's work (an item only
-            // waits for smaller tickets, so holding two cannot deadlock)
-            if (ok) next = (long long)atomicAdd(L.ticket, 1ull);
         }
         __syncthreads();
         if (!s_ok) return;
+        // the next ticket, taken now so that its round trip overlaps this item's work (an item only
+        // waits for smaller tickets, so holding two cannot deadlock)
+        if (threadIdx.x == 0) next = (long long)atomicAdd(L.ticket, 1ull);
         const KParams<T>& p = sp;
         const int nx = p.nx, nxy = p.nx * p.ny;
         const int k0 = s * sl.sz, k1 = min(k0 + sl.sz, p.nz);

@@ -221,7 +221,10 @@ struct GParams {
 #define FDTD_BATCH_MINB 2
 #endif
 constexpr int kMaxBatch = 16;          // runs of one launch
-constexpr int kBatchThreads = 256;     // threads of a block of the persistent kernel
+#ifndef FDTD_BATCH_THREADS
+#define FDTD_BATCH_THREADS 256
+#endif
+constexpr int kBatchThreads = FDTD_BATCH_THREADS;   // threads of a block of the persistent kernel
 constexpr int kMinBatchSZ = 4;         // z planes of a work item: 4 or 8 (<= kShellKZ) by grid size
 constexpr int kMaxBatchSlabs = 65536 / kMinBatchSZ + 1;
 static_assert(2 * kMinBatchSZ <= kShellKZ, "work items of up to kShellKZ planes");

@@ -16,6 +16,12 @@ Admitted requests go to one of two lanes:
   launches.
 
 Finished requests release their slot and memory immediately and the next waiting one is admitted.
+Large grids (exclusive_cells) run one at a time: each nearly fills the HBM bandwidth alone, so two of
+them side by side only slow each other, while smaller requests fill the SMs and the gaps between a large
+grid's kernels; a request may overtake one that waits for a running large grid.  Measured on a GB300,
+the persistent batch lane is slower than concurrent plain-lane requests at every grid size of the
+serving stream (12-13 against 18-35 Gcell-updates/s on 48^3-96^3 grids), so the default routes every
+request through the plain lane and the batch lane is an option (batch_max_cells).
 Each result is bitwise independent of the mix: a request's state is private, every kernel is
 deterministic, and a batched run's arithmetic does not depend on which runs share its launches.
 """
@@ -82,12 +88,18 @@ class GradientServer:
 
     max_slots requests on the device at once (at most 16 of them in the batch lane), their summed
     footprints within hbm_budget bytes.  batch_max_cells: grids with at most this many cells take the
-    batch lane (0: every request takes the plain lane; None: every FP32 request takes the batch lane).
-    chunk_steps: steps of every batched run per persistent launch; batch_blocks: blocks of those launches
-    (0: as many as fit; fewer leave SMs to the plain lane's kernels)."""
+    batch lane (0, the default: every request takes the plain lane; None: every FP32 request takes the
+    batch lane).  chunk_steps: steps of every batched run per persistent launch; batch_blocks: blocks of
+    those launches (0: as many as fit; fewer leave SMs to the plain lane's kernels).  plain_workers:
+    plain-lane requests running at once.  exclusive_cells: grids with at least this many cells run one at
+    a time (two of them side by side only share the HBM bandwidth each already nearly fills), and a
+    waiting request may overtake one that waits for such a grid to finish (None: strict FIFO).
 
-    def __init__(self, max_slots=16, hbm_budget=None, device=0, batch_max_cells=64 ** 3, chunk_steps=128,
-                 plain_workers=4, batch_blocks=0):
+    The defaults are the measured best on the seeded 200-request stream on a GB300: the plain lane for
+    every size, eight at a time, grids of 128^3 cells and more one at a time."""
+
+    def __init__(self, max_slots=16, hbm_budget=None, device=0, batch_max_cells=0, chunk_steps=128,
+                 plain_workers=8, batch_blocks=0, exclusive_cells=128 ** 3):
         import torch
         self.torch = torch
         self.device = device
@@ -98,6 +110,8 @@ class GradientServer:
         self.hbm_budget = hbm_budget
         self.max_slots = max_slots
         self.batch_max_cells = batch_max_cells
+        self.exclusive_cells = exclusive_cells
+        self.exclusive_running = 0
         self.chunk_steps = chunk_steps
         self.cv = threading.Condition()
         self.waiting = collections.deque()
@@ -164,25 +178,49 @@ class GradientServer:
             return False
         return self.batch_max_cells is None or req.cells() <= self.batch_max_cells
 
-    def _can_admit(self):
-        if not self.waiting or self.active >= self.max_slots:
-            return False
-        req, fp, _ = self.waiting[0]
+    def _exclusive(self, req):
+        return self.exclusive_cells is not None and req.cells() >= self.exclusive_cells
+
+    def _admissible(self, req, fp):
         if self.in_use + fp > self.hbm_budget:
+            return False
+        if self._exclusive(req) and self.exclusive_running > 0:
             return False
         return not self._batch_lane(req) or len(self.in_batch) + self.batch_pending < N.MAX_BATCH
 
-    def _release(self, fp):
+    def _next_index(self):
+        """Index of the request to admit next: the first waiting one, or, with exclusive_cells, the first
+        one that is admissible when the head waits for a running large grid (large grids stay in FIFO
+        order among themselves); None if none can start now."""
+        if not self.waiting or self.active >= self.max_slots:
+            return None
+        for q, (req, fp, _) in enumerate(self.waiting):
+            if self._admissible(req, fp):
+                return q
+            if self.exclusive_cells is None or not self._exclusive(req) or self.exclusive_running == 0:
+                return None        # FIFO: only a head blocked by a running large grid lets others pass
+        return None
+
+    def _can_admit(self):
+        return self._next_index() is not None
+
+    def _release(self, fp, req=None):
         with self.cv:
             self.in_use -= fp
             self.active -= 1
+            if req is not None and self._exclusive(req):
+                self.exclusive_running -= 1
             self.cv.notify_all()
 
     def _admit_one(self):
-        """Pop the first waiting request and start it in its lane (called with self.cv held)."""
-        req, fp, fut = self.waiting.popleft()
+        """Take the next admissible waiting request and start it in its lane (called with self.cv held)."""
+        q = self._next_index()
+        req, fp, fut = self.waiting[q]
+        del self.waiting[q]
         self.in_use += fp
         self.active += 1
+        if self._exclusive(req):
+            self.exclusive_running += 1
         if self._batch_lane(req):
             self.batch_pending += 1             # in the batch lane from here on (counted before its submit)
         self.peak_active = max(self.peak_active, self.active)
@@ -202,7 +240,7 @@ class GradientServer:
                 raise
         except Exception as e:
             fut.set_exception(e)
-            self._release(fp)
+            self._release(fp, req)
             return
         self.in_batch[p] = [req, fut, fp, t_admit, 0]
         self.peak_batched = max(self.peak_batched, len(self.in_batch))
@@ -218,7 +256,7 @@ class GradientServer:
         except Exception as e:  # the request fails, the server keeps serving
             fut.set_exception(e)
         finally:
-            self._release(fp)
+            self._release(fp, req)
 
     def _finish_batched(self, p, status):
         req, fut, fp, t_admit, phase = self.in_batch[p]
@@ -236,7 +274,7 @@ class GradientServer:
             fut.set_exception(e)
         del self.in_batch[p]
         p.close()
-        self._release(fp)
+        self._release(fp, req)
 
     def _loop(self):
         torch = self.torch
@@ -266,7 +304,7 @@ class GradientServer:
                 for p, (req, fut, fp, t_admit, phase) in list(self.in_batch.items()):
                     fut.set_exception(e)
                     p.close()
-                    self._release(fp)
+                    self._release(fp, req)
                 self.in_batch.clear()
                 self.batch.close()
                 self.batch = self._new_batch()

@@ -83,3 +83,17 @@ def test_requests_arriving_during_a_launch_join_the_next_one(srv):
         res = [f.result() for f in futs]
     assert all(r.lane == "batch" for r in res)
     assert server.peak_batched >= 2 and server.launches >= 2
+
+
+def test_large_grids_run_one_at_a_time_and_small_ones_overtake(srv):
+    """exclusive_cells: two large requests never overlap on the device, and a small request submitted after
+    the second large one starts before it (it may pass a request that waits for a running large grid)."""
+    big = srv.from_stream(synth.serving_stream(seed=23, n_requests=2, sizes=(64,), steps=(400, 401), pairs=(2, 2)))
+    small = srv.from_stream(synth.serving_stream(seed=29, n_requests=1, sizes=(32,), steps=(300, 301), pairs=(1, 1)))
+    with srv.GradientServer(max_slots=4, batch_max_cells=0, exclusive_cells=64 ** 3) as server:
+        futs = [server.submit(r) for r in big + small]
+        b1, b2, s1 = [f.result() for f in futs]
+    assert b2.t_admit >= b1.t_done or b1.t_admit >= b2.t_done
+    first, second = (b1, b2) if b1.t_admit <= b2.t_admit else (b2, b1)
+    assert s1.t_admit < second.t_admit
+    assert {b1.lane, b2.lane, s1.lane} == {"plain"}
