@@ -236,6 +236,12 @@ constexpr int ed_min_blocks()
 #endif
 }
 
+// L2 prefetch (no registers held) of a line a coming plane's update reads.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+#ifndef FDTD_ED_PF
+#define FDTD_ED_PF 0   // planes ahead in e_design_column (0: none)
+#endif
+
 // One component C of the (x, y) column (i, j), planes [k0, k1); returns max |E| of its samples.
 template <typename T, int MP, int C, bool CG = false>
 __device__ __forceinline__ T e_design_column(const KParams<T>& p, const PoleTable<T>& tab, int i, int j, int k0, int k1, int n)
@@ -273,6 +279,19 @@ __device__ __forceinline__ T e_design_column(const KParams<T>& p, const PoleTabl
             hb[r] = ldf<CG>(Hb + id);
             ham[r] = la > 0 ? ldf<CG>(Ha + id - oa) : T(0);
             hbm[r] = lb > 0 ? ldf<CG>(Hb + id - ob) : T(0);
+            if constexpr (!CG && FDTD_ED_PF > 0) {   // the rows of a coming plane into L2
+                if (k + FDTD_ED_PF < k1) {
+                    const unsigned ip = id + FDTD_ED_PF * plane;
+                    const long long dp = dv + FDTD_ED_PF * p.dplane;
+                    prefetch_l2(Ha + ip);
+                    prefetch_l2(Hb + ip);
+                    prefetch_l2(Ec + ip);
+                    prefetch_l2(rc + dp);
+#pragma unroll
+                    for (int pp = 0; pp < (MP > 0 ? MP : 1); ++pp)
+                        if (pp < p.P[C]) prefetch_l2(p.Q[C] + pp * p.nd + dp);
+                }
+            }
             e0[r] = ldf<CG>(Ec + id);
             ds[r] = inxy_m && k >= p.mb[C][4] && k < p.mb[C][5] && !(inxy_g && k >= p.gb[4] && k < p.gb[5]);
             rho[r] = ds[r] ? ldf<CG>(rc + dv) : T(0);
