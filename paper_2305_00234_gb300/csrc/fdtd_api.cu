@@ -757,22 +757,38 @@ struct Solver : SolverBase {
         if (r != CUDA_SUCCESS) throw Err{FDTD_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r)};
     }
 
-    // Interior box of the fused kernel: whole kTX x kTY tiles whose cells and one-cell -x/-y halo lie
-    // outside the walls and the CPML slabs, x0 a multiple of 4 (16-byte aligned TMA boxes), planes
-    // cpml_z_low + 1 .. nz - cpml_z_high - 1 (the plane below the first one is outside the slab too).
-    // Needs x rows of a multiple of 16 bytes and the tensor-map encoder.  The rest of the grid is the
-    // shell: at most six boxes.
+    // Interior box of the fused kernel: kTX x kTY tiles whose cells and one-cell -x/-y halo lie outside
+    // the walls and the CPML slabs, x0 a multiple of 4 (16-byte aligned TMA boxes), planes cpml_z_low + 1
+    // .. nz - cpml_z_high - 1 (the plane below the first one is outside the slab too).  The box reaches
+    // the +x and +y slabs: its last tile column and row may be partial (an even number of x cells; the
+    // kernel leaves the cells beyond to the shell), as long as it holds one whole tile each way
+    // (FDTD_PARTIAL_TILES 0: whole tiles only).  Needs x rows of a multiple of 16 bytes and the tensor-map
+    // encoder.  The rest of the grid is the shell: at most six boxes.
 #ifndef FDTD_STEP_MINBLK
 #define FDTD_STEP_MINBLK (2 * 152)
+#endif
+#ifndef FDTD_PARTIAL_TILES
+#define FDTD_PARTIAL_TILES 1
+#endif
+#ifndef FDTD_PARTIAL_MIN_X
+#define FDTD_PARTIAL_MIN_X 24   // x cells a partial last tile column must hold (of kTX)
+#endif
+#ifndef FDTD_PARTIAL_MIN_Y
+#define FDTD_PARTIAL_MIN_Y 12   // rows a partial last tile row must hold (of kTY)
 #endif
     void split_grid(KParams<T>& p)
     {
         const fdtd_grid_desc& d = c->d;
         const int X0 = (std::max(p.cpl[0] + 1, 1) + 3) / 4 * 4, Y0 = std::max(p.cpl[1] + 1, 1), Z0 = p.cpl[2] + 1;
-        const int ntx = (d.nx - p.cph[0] - X0) / fdtd::kTX, nty = (d.ny - p.cph[1] - Y0) / fdtd::kTY;
+        const int wx = d.nx - p.cph[0] - X0, wy = d.ny - p.cph[1] - Y0;   // widths up to the +x / +y slabs
         const int Z1 = d.nz - p.cph[2];
-        fused = ((size_t)d.nx * sizeof(T)) % 16 == 0 && ntx > 0 && nty > 0 && Z1 > Z0 && tensor_map_encoder() != nullptr;
-        const int ib[6] = {X0, X0 + ntx * fdtd::kTX, Y0, Y0 + nty * fdtd::kTY, Z0, Z1};
+        fused = ((size_t)d.nx * sizeof(T)) % 16 == 0 && wx >= fdtd::kTX && wy >= fdtd::kTY && Z1 > Z0 &&
+                tensor_map_encoder() != nullptr;
+        const int rx = (wx & ~1) % fdtd::kTX, ry = wy % fdtd::kTY;   // cells of a partial last tile
+        const int X1 = X0 + wx / fdtd::kTX * fdtd::kTX + (FDTD_PARTIAL_TILES && rx >= FDTD_PARTIAL_MIN_X ? rx : 0);
+        const int Y1 = Y0 + wy / fdtd::kTY * fdtd::kTY + (FDTD_PARTIAL_TILES && ry >= FDTD_PARTIAL_MIN_Y ? ry : 0);
+        const int ntx = (X1 - X0 + fdtd::kTX - 1) / fdtd::kTX, nty = (Y1 - Y0 + fdtd::kTY - 1) / fdtd::kTY;
+        const int ib[6] = {X0, X1, Y0, Y1, Z0, Z1};
         std::fill(p.ib, p.ib + 6, 0);
         if (fused) std::copy(ib, ib + 6, p.ib);
         // z planes per block: kKC, halved while the launch has fewer than FDTD_STEP_MINBLK blocks

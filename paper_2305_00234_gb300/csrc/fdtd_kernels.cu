@@ -135,7 +135,7 @@ static cudaError_t graph_kernel(cudaGraph_t g, cudaGraphNode_t* node, void (*k)(
 template <typename T>
 cudaError_t graph_step(cudaGraph_t g, cudaGraphNode_t* node, const KParams<T>& p, const StepMaps& m)
 {
-    const dim3 grid((p.ib[1] - p.ib[0]) / kTX, (p.ib[3] - p.ib[2]) / kTY, (p.ib[5] - p.ib[4] + p.kc - 1) / p.kc);
+    const dim3 grid((p.ib[1] - p.ib[0] + kTX - 1) / kTX, (p.ib[3] - p.ib[2] + kTY - 1) / kTY, (p.ib[5] - p.ib[4] + p.kc - 1) / p.kc);
     return graph_kernel(g, node, step_kernel<T>, grid, dim3(kPX, kTY), StepSmem<T>::total, p, m);
 }
 
@@ -191,14 +191,14 @@ cudaError_t graph_dft(cudaGraph_t g, cudaGraphNode_t* node, const DParams<T>& d,
 template <typename T>
 unsigned step_blocks(const KParams<T>& p)
 {
-    return (unsigned)((p.ib[1] - p.ib[0]) / kTX) * (unsigned)((p.ib[3] - p.ib[2]) / kTY) *
+    return (unsigned)((p.ib[1] - p.ib[0] + kTX - 1) / kTX) * (unsigned)((p.ib[3] - p.ib[2] + kTY - 1) / kTY) *
            (unsigned)((p.ib[5] - p.ib[4] + p.kc - 1) / p.kc);
 }
 
 template <typename T>
 cudaError_t launch_step(const KParams<T>& p, const StepMaps& m, cudaStream_t s, bool pdl)
 {
-    const dim3 g((p.ib[1] - p.ib[0]) / kTX, (p.ib[3] - p.ib[2]) / kTY, (p.ib[5] - p.ib[4] + p.kc - 1) / p.kc);
+    const dim3 g((p.ib[1] - p.ib[0] + kTX - 1) / kTX, (p.ib[3] - p.ib[2] + kTY - 1) / kTY, (p.ib[5] - p.ib[4] + p.kc - 1) / p.kc);
     return launch_chain(step_kernel<T>, g, dim3(kPX, kTY), StepSmem<T>::total, s, pdl, p, m);
 }
 

@@ -350,6 +350,9 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
     const int i0 = p.ib[0] + blockIdx.x * kTX, j0 = p.ib[2] + blockIdx.y * kTY;
     const int i = i0 + 2 * tx, j = j0 + ty;                            // first cell of the own pair
+    // the last tile column and row may be partial: cells beyond the box are the shell's (their H is
+    // computed here too, for nothing, but neither stored nor used by a cell of the box)
+    const bool own = i < p.ib[1] && j < p.ib[3];
     const int kb = p.ib[4] + blockIdx.z * p.kc, ke = min(kb + p.kc, p.ib[5]);
     const int k_first = kb - 1;            // >= 0: the interior box starts above plane 0
     const int ne_tot = ke - k_first + 1;   // E planes k_first .. ke
@@ -417,9 +420,11 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
             st2(sHc + on, h[0]);
             st2(sHc + PN + on, h[1]);
             st2(sHc + 2 * PN + on, h[2]);
-            st2(p.Hn[0] + id, h[0]);
-            st2(p.Hn[1] + id, h[1]);
-            st2(p.Hn[2] + id, h[2]);
+            if (own) {
+                st2(p.Hn[0] + id, h[0]);
+                st2(p.Hn[1] + id, h[1]);
+                st2(p.Hn[2] + id, h[2]);
+            }
             // halo work goes to three different warps (the second half of warps 7, 6 and 5), so that
             // no warp carries more than one extra cell update per plane
             if (ty == kTY - 1) {                           // -y halo row, as pairs
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(kPX * kTY, StepCfg<T>::MINB)
             if (e_issued < ne_tot) issue_e(e_issued++);
             if (h_issued < nh_tot) issue_h(h_issued++);
         }
-        if (r > 0) {
+        if (r > 0 && own) {
             if (lite)
                 e_pair<T, true>(p, sHc, on, i, j, k, n, eup, hinc_n, e0, h, hxp, hyp, id, check, emax);
             else

@@ -98,13 +98,14 @@ def two_dispersive(prec, steps=400, seed=5, gamma=2e6):
 
 
 @pytest.mark.parametrize("src", ["tfsf", "dipole_shell", "dipole_interior"])
-@pytest.mark.parametrize("prec,nx,fused", [(32, 52, 1), (32, 45, 0), (64, 46, 1), (64, 45, 0)])
+@pytest.mark.parametrize("prec,nx,fused", [(32, 52, 1), (32, 45, 0), (64, 46, 1), (64, 45, 0), (32, 72, 1), (64, 72, 1)])
 def test_step_paths(gpu, prec, nx, fused, src):
     """Both background-step layouts: an interior box for the fused TMA kernel (x rows a multiple of
     16 bytes) plus the shell kernels around it, and the shell kernels over the whole grid.  Grids
     ragged in all three tile axes, CPML of unequal thickness, a 3-pair metal whose design box
     straddles the interior box, and the TF/SF plane inside the interior box or a dipole in the shell or
-    in the interior box."""
+    in the interior box.  nx = 72: the interior box ends in a partial tile column (26 of 32 cells) and,
+    like nx = 52, a partial tile row (14 of 16 rows)."""
     kw = {"tfsf": dict(src_kind=1, src_pos=(9, 0, 0)),
           "dipole_shell": dict(src_kind=0, src_comp=1, src_pos=(8, 33, 6)),
           "dipole_interior": dict(src_kind=0, src_comp=2, src_pos=(12, 8, 8))}[src]
