@@ -238,6 +238,9 @@ constexpr int ed_min_blocks()
 
 // L2 prefetch (no registers held) of a line a coming plane's update reads.
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+#ifndef FDTD_DFT_PF
+#define FDTD_DFT_PF 1   // 1: dft_voxel prefetches its accumulators into L2 first (config 2: 0.243 -> 0.212 ms)
+#endif
 #ifndef FDTD_ED_PF
 #define FDTD_ED_PF 0   // planes ahead in e_design_column (0: none)
 #endif
@@ -353,6 +356,10 @@ __global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_ke
 template <typename T, bool CG>
 __device__ __forceinline__ void dft_voxel(const DParams<T>& d, long long v, int n0, int cnt)
 {
+#if FDTD_DFT_PF
+    if constexpr (!CG)   // the FP64 accumulators into L2 while the snapshots load
+        for (int q = 0; q < 3 * d.nf; ++q) prefetch_l2(d.dft + (long long)q * d.nd + v);
+#endif
     T e[kMaxSnap][3];
 #pragma unroll
     for (int s = 0; s < kMaxSnap; ++s) {
