@@ -58,8 +58,10 @@ def test_autograd_config4_fp64_vs_oracle_and_fd(lib):
     fd = np.array(fd)
     ga = np.array([g[v] for v in vox])
     err = np.abs(ga - fd) / np.abs(fd).max()
-    # the frequency-domain adjoint is exact for decayed fields; 2000 steps leave a small tail
-    assert np.median(err) < 2e-2, (np.median(err), err.max())
+    # the frequency-domain adjoint is exact for decayed fields; 2000 steps leave a small tail (measured on a
+    # GB300: the median voxel within 1e-5 of the largest derivative, the worst within 10%)
+    assert np.median(err) < 1e-4, (np.median(err), err.max())
+    assert err.max() < 0.2, (np.median(err), err.max())
     assert np.corrcoef(ga, fd)[0, 1] > 0.999
     dft, hist = lib.checkpoint_bytes(p)
     assert dft * 100 < hist
