@@ -759,9 +759,10 @@ struct Solver : SolverBase {
 
     // Interior box of the fused kernel: kTX x kTY tiles whose cells and one-cell -x/-y halo lie outside
     // the walls and the CPML slabs, x0 a multiple of 4 (16-byte aligned TMA boxes), planes cpml_z_low + 1
-    // .. nz - cpml_z_high - 1 (the plane below the first one is outside the slab too).  The box reaches
-    // the +x and +y slabs: its last tile column and row may be partial (an even number of x cells; the
-    // kernel leaves the cells beyond to the shell), as long as it holds one whole tile each way
+    // .. nz - cpml_z_high - 1 (the plane below the first one is outside the slab too), at least one whole
+    // tile each way.  Toward the +x and +y slabs the box ends in a partial tile column or row (an even
+    // number of x cells; the kernel leaves the cells beyond to the shell) when that tile holds at least
+    // FDTD_PARTIAL_MIN_X columns / FDTD_PARTIAL_MIN_Y rows: a partial tile costs a whole tile's work
     // (FDTD_PARTIAL_TILES 0: whole tiles only).  Needs x rows of a multiple of 16 bytes and the tensor-map
     // encoder.  The rest of the grid is the shell: at most six boxes.
 #ifndef FDTD_STEP_MINBLK

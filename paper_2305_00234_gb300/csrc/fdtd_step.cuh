@@ -3,9 +3,10 @@
 // the TF/SF correction and point sources), reading E^n / H^{n-1/2} from one buffer of each pair and
 // writing the other.  The grid is split in two:
 //
-// * an interior box of whole tiles, away from the walls and the CPML slabs, updated by step_kernel in
-//   one pass: 48 B per cell (each field word read once and written once) instead of the 72 B of
-//   separate H and E passes.  A block owns a kTX x kTY tile and marches through kKC z planes (plus the
+// * an interior box of tiles (the last column or row may be partial), away from the walls and the CPML
+//   slabs, updated by step_kernel in one pass: 48 B per cell (each field word read once and written
+//   once) instead of the 72 B of separate H and E passes.  A block owns a kTX x kTY tile and marches
+//   through p.kc (at most kKC) z planes (plus the
 //   plane below, whose H is the z-1 neighbour of the first E update); each thread updates two
 //   x-adjacent cells with paired FP32 arithmetic (one instruction for both cells) and 8-byte shared /
 //   global accesses.  Per plane, TMA brings E^n and H^{n-1/2} of the tile plus a one-cell halo into
