@@ -557,7 +557,9 @@ struct Solver : SolverBase {
         p.nblocks_s = fdtd::shell_blocks(shell);
         p.edz = 1;
         p.ed_pair = design_pairable() ? 1 : 0;
-        p.nblocks_d = c->nd ? fdtd::design_blocks(p.ed_pair ? c->dn[0] / 2 : c->dn[0], c->dn[1], c->dn[2], p.edz) : 0;
+        p.nblocks_d = c->nd ? fdtd::design_blocks(p.ed_pair ? c->dn[0] / 2 : c->dn[0], c->dn[1], c->dn[2], p.edz,
+                                                  FDTD_ED_FLAT && !p.ed_pair)
+                            : 0;
         p.nblocks_e = p.nblocks_s + p.nblocks_d;
         p.blowup = (T)1e30;
         p.n_steps = d.n_steps;

@@ -158,6 +158,9 @@ template <typename T>
 static dim3 design_grid(const KParams<T>& p)
 {
     const dim3 g3 = grid3((p.db[1] - p.db[0]) / (p.ed_pair ? 2 : 1), p.db[3] - p.db[2], p.db[5] - p.db[4]);
+    const unsigned nxy = (unsigned)(p.db[1] - p.db[0]) * (unsigned)(p.db[3] - p.db[2]);
+    if (FDTD_ED_FLAT && !p.ed_pair)
+        return dim3((nxy + kBX * kBY - 1) / (kBX * kBY), 1, 3 * ((g3.z + p.edz - 1) / p.edz));
     return dim3(g3.x, g3.y, 3 * ((g3.z + p.edz - 1) / p.edz));
 }
 
@@ -279,12 +282,13 @@ cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s, bool pdl)
 #ifndef FDTD_ED_MINCOLS
 #define FDTD_ED_MINCOLS (5 * 152)
 #endif
-unsigned design_blocks(int dnx, int dny, int dnz, int& edz)
+unsigned design_blocks(int dnx, int dny, int dnz, int& edz, bool flat)
 {
     const dim3 g = grid3(dnx, dny, dnz);
+    const unsigned gxy = flat ? ((unsigned)dnx * (unsigned)dny + kBX * kBY - 1) / (kBX * kBY) : g.x * g.y;
     unsigned t = 0;
     for (edz = kEdZ;; edz = (edz + 1) / 2) {
-        t = g.x * g.y * 3 * ((g.z + edz - 1) / edz);
+        t = gxy * 3 * ((g.z + edz - 1) / edz);
         if (t >= FDTD_ED_MINCOLS || edz == 1) break;
     }
     return t;

@@ -331,8 +331,17 @@ template <typename T, int MP>
 __global__ void __launch_bounds__(kBX * kBY, ed_min_blocks<T, MP>()) e_design_kernel(const KParams<T> p, const PoleTable<T> tab)
 {
     const int zc = blockIdx.z / 3, c = blockIdx.z - 3 * zc;
-    const int i = p.db[0] + blockIdx.x * kBX + threadIdx.x;
-    const int j = p.db[2] + blockIdx.y * kBY + threadIdx.y;
+    int i, j;
+    if (FDTD_ED_FLAT) {   // columns in row order, kBX * kBY per block
+        const int dnx = p.db[1] - p.db[0];
+        const int col = blockIdx.x * (kBX * kBY) + threadIdx.y * kBX + threadIdx.x;
+        const int y = col / dnx;
+        i = p.db[0] + (col - y * dnx);
+        j = p.db[2] + y;
+    } else {
+        i = p.db[0] + blockIdx.x * kBX + threadIdx.x;
+        j = p.db[2] + blockIdx.y * kBY + threadIdx.y;
+    }
     const int k0 = p.db[4] + zc * p.edz, k1 = min(p.db[5], k0 + p.edz);
     pdl_wait();
     pdl_trigger();

@@ -31,7 +31,7 @@ cudaError_t launch_dft(const DParams<T>& d, int cnt, cudaStream_t s, bool pdl = 
 unsigned shell_blocks(ShellBoxes& s);   // fills s.first, returns the launch's blocks
 template <typename T>
 cudaError_t launch_shell(const KParams<T>& p, const ShellBoxes& s, bool e_part, cudaStream_t st, bool pdl = false);
-unsigned design_blocks(int dnx, int dny, int dnz, int& edz);   // also picks the column depth
+unsigned design_blocks(int dnx, int dny, int dnz, int& edz, bool flat);   // also picks the column depth
 template <typename T>
 cudaError_t launch_grad(const GParams<T>& g, unsigned nblocks, cudaStream_t s);
 cudaError_t launch_gap_gather(const double2* dft, long long nd, int nf, const int* db, int dnx, int dny, const int* gb,
